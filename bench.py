@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Throughput of the fast direct high-order FEM Poisson solver on GB300.
+
+Metric: unknowns solved per second on one GB300, 2D unit square, n = 9, K = 1024
+elements per axis (9215^2 = 84,916,225 unknowns), at 1e-12 relative L2 error: the
+mixed path (FP32 transform sweeps + FP64 matrix-free residual refinement) timed as the
+headline `value`, the plain FP64 GPU path beside it.  One step = one hofem_solve of
+the whole problem (all sweeps and refinement steps).  Inputs: one seeded smooth RHS
+(16 random sine modes + uniform noise) resident in HBM; 680 MB per FP64 array, larger
+than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own problem on its own GPU (weak scaling, no
+collective); rank 0 prints one JSON line.  `--impl reference` times the CPU oracle on
+the host cores (there is no other reference implementation of this method).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ORDER, K_ELEM, X_LEN = 9, 1024, 1.0
+M_AXIS = N_ORDER * K_ELEM - 1
+UNKNOWNS = M_AXIS * M_AXIS
+METRIC = "unknowns solved/s on 1 GB300 (2D n=9 K=1024; mixed vs FP64 at 1e-12 rel err)"
+UNIT = "unknowns/s"
+PAPER_UNKNOWNS_PER_S = 84916225 / 120.0   # paper: < 2 min on a laptop (context only)
+WORKLOAD = "2D unit square, n=9 Lagrange elements, K=1024 per axis, 9215^2 = 84,916,225 unknowns, 1 RHS"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--refine-iters", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def load_traffic(kind):
+    """DRAM bytes per launch of `kind` from the committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        data = json.load(open(path))
+        ent = data.get(kind)
+        if not ent:
+            return None
+        import hashlib
+        src = os.path.join(ROOT, "paper_1609_07758_gb300", "csrc", ent["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != ent["source_sha"]:
+            return None
+        return ent["bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def oracle_sample(steps=1):
+    """The CPU oracle on the host cores: dense mode products of the tensor-product solve."""
+    from oracle import solve as osolve
+    from oracle import spectrum
+    from paper_1609_07758_gb300 import inputs
+    f = inputs.smooth_sine_rhs(2, N_ORDER, K_ELEM)
+    spec = spectrum.spectrum(N_ORDER, K_ELEM, X_LEN)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        osolve.solve_tensor(f, [N_ORDER, N_ORDER], [K_ELEM, K_ELEM], [X_LEN, X_LEN], 0.0, specs=[spec, spec])
+    dt = (time.perf_counter() - t0) / steps
+    return UNKNOWNS / dt, dt
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import solve as osolve
+    from oracle import spectrum
+    from paper_1609_07758_gb300 import inputs
+    f = inputs.smooth_sine_rhs(2, N_ORDER, K_ELEM)[0]
+    spec = spectrum.spectrum(N_ORDER, K_ELEM, X_LEN)
+    S = spec.dense_S()
+    # one step = one of the four dense 9215^3 mode products of the oracle's solve (1/4 of it)
+    def step(i):
+        if i % 2 == 0:
+            return osolve._mode(f[None], S, 1)
+        return osolve._mode(f[None], S.T, 2)
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(i)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = UNKNOWNS / (4.0 * dt)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "each step = one of the 4 dense 9215^3 FP64 mode products of the "
+                                   "oracle's tensor-product solve; value = unknowns / (4 x step time)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import torch
+    import paper_1609_07758_gb300 as hofem
+    from paper_1609_07758_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    f_host = inputs.smooth_sine_rhs(2 + rank, N_ORDER, K_ELEM)
+    f = torch.from_numpy(f_host).cuda()
+    u = torch.empty_like(f)
+    u64 = torch.empty_like(f)
+    K2, X2 = [K_ELEM, K_ELEM], [X_LEN, X_LEN]
+    plan = hofem.Plan(2, K2, N_ORDER, X2, hofem.HOFEM_FP32_REFINED)
+    plan.set_refinement(args.refine_iters)
+    plan.reserve(1)
+    plan64 = hofem.Plan(2, K2, N_ORDER, X2, hofem.HOFEM_FP64)
+
+    # accuracy of the mixed solve against the plain FP64 GPU solve (oracle parity is in tests/)
+    plan64.solve(f, u64, 1, stream)
+    plan.solve(f, u, 1, stream)
+    torch.cuda.synchronize()
+    rel_mixed_vs_fp64 = float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))
+    last_update = plan.info().last_rel_update
+
+    def timed(pl, out, steps, warmup):
+        for _ in range(warmup):
+            pl.solve(f, out, 1, stream)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches0 = pl.info().kernel_launches
+        e0.record(stream)
+        for _ in range(steps):
+            pl.solve(f, out, 1, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = e0.elapsed_time(e1) / steps
+        return ms, pl.info().kernel_launches - launches0
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_mixed, launches = timed(plan, u, args.steps, args.warmup)
+    ms_fp64, _ = timed(plan64, u64, max(3, args.steps // 4), 1)
+    clock_info = clocks.stop()
+    ms_mixed = max_over_ranks(ms_mixed, world)
+    ms_fp64 = max_over_ranks(ms_fp64, world)
+
+    # per-kernel device time (events on the launching stream around every kernel)
+    plan.profile(1)
+    for _ in range(max(3, args.steps // 3)):
+        plan.solve(f, u, 1, stream)
+    prof = plan.get_profile()
+    plan.profile(0)
+    kinds = {k: {"launches": v[0], "ms_per_launch": v[1] / v[0], "total_ms": v[1]} for k, v in prof.items()}
+    dominant = max(kinds, key=lambda k: kinds[k]["total_ms"])
+
+    # end to end through the C ABI with host buffers: H2D of f, solve, D2H of u, every step
+    fh = torch.from_numpy(f_host).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    fd = torch.empty_like(f)
+    ud = torch.empty_like(f)
+
+    def e2e_step():
+        fd.copy_(fh, non_blocking=True)
+        plan.solve(fd, ud, 1, stream)
+        uh.copy_(ud, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world)
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    n1 = N_ORDER + 1
+    # algorithmic work per launch (per unknown x unknowns): see DESIGN.md, "Rooflines"
+    fp64_flops_apply = 2 * 2 * n1 * n1 / N_ORDER * UNKNOWNS       # two sum-factorised 1D products
+    sweep_bytes = {"sweep_fwd_f32": 12.0, "sweep_fsi_f32": 8.0, "sweep_inv_f32": 20.0,
+                   "sweep_fwd_f64": 16.0, "sweep_fsi_f64": 16.0, "sweep_inv_f64": 16.0}
+    d = kinds[dominant]
+    sec = d["ms_per_launch"] / 1e3
+    if dominant == "apply_f64":
+        achieved = fp64_flops_apply / sec / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": achieved / 1.25, "traffic": load_traffic(dominant), "kernel": dominant,
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe); measured FMA probe 1.20 TFLOP/s"}
+    else:
+        achieved = sweep_bytes[dominant] * UNKNOWNS / sec / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": load_traffic(dominant), "kernel": dominant,
+                "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, dt = oracle_sample(1)
+        cpu = {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one full oracle solve of the same workload (dense FP64 mode products with the "
+                         f"60-digit eigenvectors, {dt:.1f} s); eigen-data precompute excluded"}
+
+    value = world * UNKNOWNS / (ms_mixed / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_UNKNOWNS_PER_S, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": 2, "n": N_ORDER, "K": [K_ELEM, K_ELEM], "unknowns": UNKNOWNS,
+                   "nrhs": 1, "path": "FP32 sweeps + FP64 residual refinement",
+                   "refine_iters": args.refine_iters, "l2": "inputs larger than L2 (680 MB FP64 arrays)",
+                   "parallelism": f"{world} independent problems (one per GPU)"},
+        "fp64_plain": {"value": world * UNKNOWNS / (ms_fp64 / 1e3), "ms_per_step": ms_fp64},
+        "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed,
+        "accuracy": {"rel_l2_mixed_vs_fp64": rel_mixed_vs_fp64, "last_rel_update": last_update},
+        "roofline": roof,
+        "kernels": kinds,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * UNKNOWNS / (ms_e2e / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * UNKNOWNS, "d2h_bytes_per_step": 8 * UNKNOWNS},
+        "gpu_launches": launches,
+        "clocks": clock_info,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,148 @@
+/*
+ * hofem.h -- C ABI of a GB300 (sm_103a) fast direct solver for n-th order Lagrange
+ * finite-element Dirichlet Poisson problems on 2D/3D boxes, after Zlotnik & Zlotnik,
+ * "A direct fast FFT-based implementation for high order finite element method on
+ * rectangular parallelepipeds for PDE" (arXiv:1609.07758).
+ *
+ * The discrete problem (Eq. bvp glob 2):
+ *     ( sum_i 4 h_i^-2 A_i (x) prod_{m!=i} C_m  +  alpha C_1 (x) ... (x) C_N ) v = f,
+ * with A_i, C_i the scaled global stiffness / mass matrices of axis i (Eq. eig_glob),
+ * h_i = X_i / K_i, and f = f^h the load vector in the same scaling (the "FEM average").
+ * It is solved by algorithm (a) of Sect. 2 par. 4: direct F_n-transforms (Theorem 2,
+ * part 2) along every axis, division by sum_i 4 h_i^-2 lambda_i + alpha (Eq. decomp v 2),
+ * inverse F_n-transforms (Theorem 2, part 1).
+ *
+ * Conventions shared by every entry point
+ *  - Arrays are FP64, C-order, shape (nrhs, M_1, ..., M_N), M_i = n K_i - 1.  Along an
+ *    axis, unknown p = (j-1) n + (i-1) is local point i (1..n) of element j (1..K);
+ *    i = n is the mesh node x_j.  So p sits at coordinate (p + 1) h / n.
+ *  - Pointers named f, u, r, in, out are DEVICE pointers owned by the caller; the
+ *    plan owns its tables and workspace.  `stream` is a cudaStream_t (NULL = legacy
+ *    default stream); every call is asynchronous on it and returns after enqueueing.
+ *  - Every call returns a status and never aborts.  On error nothing is enqueued
+ *    unless the status is HOFEM_ERR_CUDA (a launch failed part-way).
+ *    hofem_last_error() gives a one-line message for the calling thread.
+ *  - A plan may be used from one host thread at a time.
+ */
+#ifndef HOFEM_H
+#define HOFEM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hofem_plan_s* hofem_plan_t;
+typedef struct hofem_batch_s* hofem_batch_t;
+
+typedef enum {
+  HOFEM_OK = 0,
+  HOFEM_ERR_INVALID_ARG = 1,
+  HOFEM_ERR_UNSUPPORTED = 2,
+  HOFEM_ERR_OOM = 3,
+  HOFEM_ERR_CUDA = 4,
+  HOFEM_ERR_NOT_CONVERGED = 5,
+  HOFEM_ERR_TIMEOUT = 6
+} hofem_status;
+
+/* Arithmetic of the transform sweeps.  *_REFINED: low-precision solves corrected by
+ * iterative refinement with an FP64 matrix-free residual r = f - A u (Eq. bvp glob 2). */
+typedef enum {
+  HOFEM_FP64 = 0,
+  HOFEM_FP32 = 1,
+  HOFEM_FP32_REFINED = 4
+} hofem_dtype;
+
+typedef struct {
+  int N;                    /* dimensions */
+  int n;                    /* element order */
+  int K[3];                 /* elements per axis */
+  int M[3];                 /* unknowns per axis, n K - 1 */
+  int dtype;                /* hofem_dtype of the plan */
+  int refine_iters;         /* residual + correction steps per solve (refined dtypes) */
+  int iterations;           /* steps actually run by the last solve */
+  int converged;            /* 1 if the last solve met its tolerance (or ran its fixed count) */
+  double last_rel_update;   /* ||delta||_2 / ||u||_2 of the last correction, max over RHS
+                               (valid after the caller synchronises the stream) */
+  double plan_ms;           /* host wall time of hofem_plan */
+  size_t table_bytes;       /* device bytes of eigen / twiddle tables */
+  size_t workspace_bytes;   /* device bytes of solve workspace currently reserved */
+  int lines_per_cta[3];     /* launch configuration chosen per axis (W) */
+  int threads_per_cta;
+  long long kernel_launches; /* kernels this plan has launched since it was created */
+} hofem_info;
+
+/* Per-kernel-kind device time, from CUDA events recorded on the launching stream around
+ * every kernel while profiling is enabled (see hofem_profile). */
+typedef struct {
+  char name[32];            /* e.g. "sweep_fwd_f32", "apply_f64" */
+  int launches;
+  double total_ms;
+} hofem_kernel_time;
+
+/* Build a plan: N = 2 or 3 axes, K[i] >= 2 elements (power of two, <= 8192) and length
+ * X[i] > 0 per axis, order 1 <= n <= 16, alpha > -pi^2 sum_i X_i^-2 (Sect. 2 par. 4).
+ * Computes, on the GPU in double-double arithmetic, the 1D eigen-data of every axis:
+ * for k = 1..K-1 the n eigenpairs of the theta-family of Theorem 1 part 3, for k = 0 the
+ * element eigenpairs of Lemma 1 (Theorem 1 part 2).  Synchronous; allocates tables. */
+hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, double alpha,
+                        hofem_plan_t* out);
+
+/* Refined dtypes only: iters = residual/correction steps after the first low-precision
+ * solve (0..16, default 2); tol > 0 additionally stops early once ||delta||/||u|| <= tol,
+ * which synchronises the stream once per step.  tol = 0 keeps a fixed count (capturable). */
+hofem_status hofem_set_refinement(hofem_plan_t plan, int iters, double tol);
+
+/* Reserve workspace for nrhs right-hand sides (solve allocates on demand otherwise;
+ * call this before capturing a solve in a CUDA graph). */
+hofem_status hofem_reserve(hofem_plan_t plan, int nrhs);
+
+/* u = A^{-1} f for nrhs right-hand sides (algorithm (a), Sect. 2 par. 4).  f, u: device
+ * FP64 arrays (nrhs, M_1..M_N); u is overwritten; f is not modified.  f == u (in place)
+ * is allowed for unrefined dtypes only. */
+hofem_status hofem_solve(hofem_plan_t plan, const double* f, double* u, int nrhs, void* stream);
+
+/* r = A u: the matrix-free FP64 operator of Eq. bvp glob 2 (stiffness applied to
+ * differences so that constants stay in its kernel exactly).  u, r: device FP64. */
+hofem_status hofem_apply(hofem_plan_t plan, const double* u, double* r, int nrhs, void* stream);
+
+/* r = f - A u, the FP64 residual used by iterative refinement.  f, u, r: device FP64. */
+hofem_status hofem_residual(hofem_plan_t plan, const double* f, const double* u, double* r,
+                            int nrhs, void* stream);
+
+/* Test hook: the 1D F_n-transform of `lines` contiguous lines of length M_axis.
+ * inverse = 0: direct transform (Theorem 2 part 2) of y: out_q = (y, s_q) / K, with the
+ * eigenvectors s_q normalised to ||s_q||_C^2 = K (so for y = C w it returns the
+ * coefficients of w).  inverse = 1: out = sum_q in_q s_q (Theorem 2 part 1).
+ * Spectral order q = (k-1) n + (l-1) for k = 1..K-1, l = 1..n (ascending lambda within
+ * k), then q = n (K-1) + (l-1), l = 1..n-1 for k = 0.  Signs: the nodal amplitude of
+ * s_q is positive for k >= 1; e^(l) has its first component of magnitude >= 1e-3 max|e|
+ * positive.  Runs in the plan's transform precision.  in, out: device FP64. */
+hofem_status hofem_transform1d(hofem_plan_t plan, int axis, int inverse, const double* in,
+                               double* out, long lines, void* stream);
+
+/* Test hook: copy axis `axis`'s eigen-data to HOST buffers (any may be NULL):
+ * lam[M] true eigenvalues 4 h^-2 lambda_q in spectral order; mix[(K-1) n n]: row l of
+ * block k-1 is (q_1..q_{n-1}, c) of mode (k, l) (interior values then the nodal
+ * amplitude, ||s||_C^2 = K); evec[(n-1)(n-1)]: row l is e^(l).  Synchronous. */
+hofem_status hofem_get_eigen(hofem_plan_t plan, int axis, double* lam, double* mix, double* evec);
+
+hofem_status hofem_get_info(hofem_plan_t plan, hofem_info* out);
+
+/* enable != 0: record a CUDA event pair around each kernel the plan launches (adds two
+ * event records per launch); enable == 0 stops recording.  Either call clears the totals. */
+hofem_status hofem_profile(hofem_plan_t plan, int enable);
+
+/* Synchronise the recorded events and return up to max_entries per-kind totals since the
+ * last hofem_profile call; *count receives the number of kinds.  out is a HOST array. */
+hofem_status hofem_get_profile(hofem_plan_t plan, hofem_kernel_time* out, int max_entries, int* count);
+void hofem_destroy(hofem_plan_t plan);
+
+const char* hofem_status_string(int status);
+const char* hofem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOFEM_H */

@@ -1,0 +1,247 @@
+"""ctypes binding of include/hofem.h -- argument marshalling only.
+
+Functions carry the C names.  Array arguments accept ``torch.Tensor`` (CUDA, float64,
+contiguous; the data pointer is passed) or raw integer device pointers; ``stream``
+accepts a ``torch.cuda.Stream``, an integer handle or None (legacy default stream).
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_NAME = "libhofem.so"
+
+HOFEM_FP64 = 0
+HOFEM_FP32 = 1
+HOFEM_FP32_REFINED = 4
+
+EXPORTED = (
+    "hofem_plan", "hofem_set_refinement", "hofem_reserve", "hofem_solve", "hofem_apply",
+    "hofem_residual", "hofem_transform1d", "hofem_get_eigen", "hofem_get_info",
+    "hofem_destroy", "hofem_status_string", "hofem_last_error", "hofem_profile", "hofem_get_profile",
+)
+
+
+class HofemError(RuntimeError):
+    def __init__(self, status, where, message):
+        self.status = status
+        super().__init__(f"{where}: {status_name(status)}: {message}")
+
+
+class hofem_info(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int), ("n", ctypes.c_int), ("K", ctypes.c_int * 3), ("M", ctypes.c_int * 3),
+        ("dtype", ctypes.c_int), ("refine_iters", ctypes.c_int), ("iterations", ctypes.c_int),
+        ("converged", ctypes.c_int), ("last_rel_update", ctypes.c_double), ("plan_ms", ctypes.c_double),
+        ("table_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
+        ("lines_per_cta", ctypes.c_int * 3), ("threads_per_cta", ctypes.c_int),
+        ("kernel_launches", ctypes.c_longlong),
+    ]
+
+
+class hofem_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path():
+    return os.environ.get("HOFEM_LIBRARY", os.path.join(HERE, "lib", _LIB_NAME))
+
+
+def load_library():
+    """Load libhofem.so (raises HofemError if it is missing -- no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise HofemError(2, "load_library", f"{path} not found; run paper_1609_07758_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    P, I, D, L, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long, ctypes.c_void_p
+    lib.hofem_plan.argtypes = [I, ctypes.POINTER(I), I, ctypes.POINTER(D), I, D, ctypes.POINTER(P)]
+    lib.hofem_set_refinement.argtypes = [P, I, D]
+    lib.hofem_reserve.argtypes = [P, I]
+    lib.hofem_solve.argtypes = [P, V, V, I, V]
+    lib.hofem_apply.argtypes = [P, V, V, I, V]
+    lib.hofem_residual.argtypes = [P, V, V, V, I, V]
+    lib.hofem_transform1d.argtypes = [P, I, I, V, V, L, V]
+    lib.hofem_get_eigen.argtypes = [P, I, V, V, V]
+    lib.hofem_get_info.argtypes = [P, ctypes.POINTER(hofem_info)]
+    lib.hofem_profile.argtypes = [P, I]
+    lib.hofem_get_profile.argtypes = [P, ctypes.POINTER(hofem_kernel_time), I, ctypes.POINTER(I)]
+    lib.hofem_destroy.argtypes = [P]
+    lib.hofem_destroy.restype = None
+    lib.hofem_status_string.argtypes = [I]
+    lib.hofem_status_string.restype = ctypes.c_char_p
+    lib.hofem_last_error.argtypes = []
+    lib.hofem_last_error.restype = ctypes.c_char_p
+    for name in ("hofem_plan", "hofem_set_refinement", "hofem_reserve", "hofem_solve", "hofem_apply",
+                 "hofem_residual", "hofem_transform1d", "hofem_get_eigen", "hofem_get_info",
+                 "hofem_profile", "hofem_get_profile"):
+        getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+_NAMES = {0: "HOFEM_OK", 1: "HOFEM_ERR_INVALID_ARG", 2: "HOFEM_ERR_UNSUPPORTED", 3: "HOFEM_ERR_OOM",
+          4: "HOFEM_ERR_CUDA", 5: "HOFEM_ERR_NOT_CONVERGED", 6: "HOFEM_ERR_TIMEOUT"}
+
+
+def status_name(status):
+    return _NAMES.get(int(status), str(status))
+
+
+def hofem_status_string(status):
+    return load_library().hofem_status_string(int(status)).decode()
+
+
+def hofem_last_error():
+    return load_library().hofem_last_error().decode()
+
+
+def _check(status, where):
+    if status != 0:
+        raise HofemError(status, where, hofem_last_error())
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        import torch
+        if not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+            raise HofemError(1, "argument", "arrays must be contiguous CUDA float64 tensors")
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a device pointer")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def hofem_plan(N, K, n, X, dtype=HOFEM_FP64, alpha=0.0):
+    lib = load_library()
+    out = ctypes.c_void_p()
+    Ka = (ctypes.c_int * N)(*[int(k) for k in K])
+    Xa = (ctypes.c_double * N)(*[float(x) for x in X])
+    _check(lib.hofem_plan(int(N), Ka, int(n), Xa, int(dtype), float(alpha), ctypes.byref(out)), "hofem_plan")
+    return out.value
+
+
+def hofem_set_refinement(plan, iters, tol=0.0):
+    _check(load_library().hofem_set_refinement(plan, int(iters), float(tol)), "hofem_set_refinement")
+
+
+def hofem_reserve(plan, nrhs):
+    _check(load_library().hofem_reserve(plan, int(nrhs)), "hofem_reserve")
+
+
+def hofem_solve(plan, f, u, nrhs, stream=None):
+    _check(load_library().hofem_solve(plan, _ptr(f), _ptr(u), int(nrhs), _stream(stream)), "hofem_solve")
+
+
+def hofem_apply(plan, u, r, nrhs, stream=None):
+    _check(load_library().hofem_apply(plan, _ptr(u), _ptr(r), int(nrhs), _stream(stream)), "hofem_apply")
+
+
+def hofem_residual(plan, f, u, r, nrhs, stream=None):
+    _check(load_library().hofem_residual(plan, _ptr(f), _ptr(u), _ptr(r), int(nrhs), _stream(stream)),
+           "hofem_residual")
+
+
+def hofem_transform1d(plan, axis, inverse, x, y, lines, stream=None):
+    _check(load_library().hofem_transform1d(plan, int(axis), int(inverse), _ptr(x), _ptr(y), int(lines),
+                                            _stream(stream)), "hofem_transform1d")
+
+
+def hofem_get_eigen(plan, axis):
+    """Host copies (lam[M], mix[K-1, n, n], evec[n-1, n-1]) of one axis' eigen-data."""
+    import numpy as np
+    info = hofem_get_info(plan)
+    n, K, M = info.n, info.K[axis], info.M[axis]
+    lam = np.zeros(M)
+    mix = np.zeros((K - 1, n, n))
+    evec = np.zeros((max(n - 1, 1), max(n - 1, 1)))
+    _check(load_library().hofem_get_eigen(plan, int(axis), lam.ctypes.data, mix.ctypes.data,
+                                          evec.ctypes.data), "hofem_get_eigen")
+    return lam, mix, evec[: n - 1, : n - 1]
+
+
+def hofem_get_info(plan):
+    info = hofem_info()
+    _check(load_library().hofem_get_info(plan, ctypes.byref(info)), "hofem_get_info")
+    return info
+
+
+def hofem_profile(plan, enable):
+    _check(load_library().hofem_profile(plan, int(enable)), "hofem_profile")
+
+
+def hofem_get_profile(plan):
+    """{kernel kind: (launches, total_ms)} since the last hofem_profile call (synchronises)."""
+    arr = (hofem_kernel_time * 16)()
+    cnt = ctypes.c_int()
+    _check(load_library().hofem_get_profile(plan, arr, 16, ctypes.byref(cnt)), "hofem_get_profile")
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(min(cnt.value, 16))}
+
+
+def hofem_destroy(plan):
+    if plan:
+        load_library().hofem_destroy(plan)
+
+
+class Plan:
+    """Owns a hofem plan handle (destroyed with the object)."""
+
+    def __init__(self, N, K, n, X, dtype=HOFEM_FP64, alpha=0.0):
+        self.handle = hofem_plan(N, K, n, X, dtype, alpha)
+        self.N, self.K, self.n, self.X, self.dtype, self.alpha = N, list(K), n, list(X), dtype, alpha
+        self.M = [n * k - 1 for k in K]
+
+    def solve(self, f, u, nrhs, stream=None):
+        hofem_solve(self.handle, f, u, nrhs, stream)
+
+    def apply(self, u, r, nrhs, stream=None):
+        hofem_apply(self.handle, u, r, nrhs, stream)
+
+    def residual(self, f, u, r, nrhs, stream=None):
+        hofem_residual(self.handle, f, u, r, nrhs, stream)
+
+    def transform1d(self, axis, inverse, x, y, lines, stream=None):
+        hofem_transform1d(self.handle, axis, inverse, x, y, lines, stream)
+
+    def set_refinement(self, iters, tol=0.0):
+        hofem_set_refinement(self.handle, iters, tol)
+
+    def reserve(self, nrhs):
+        hofem_reserve(self.handle, nrhs)
+
+    def info(self):
+        return hofem_get_info(self.handle)
+
+    def profile(self, enable):
+        hofem_profile(self.handle, enable)
+
+    def get_profile(self):
+        return hofem_get_profile(self.handle)
+
+    def eigen(self, axis):
+        return hofem_get_eigen(self.handle, axis)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hofem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,619 @@
+// C ABI of the hofem library: plans, solves, the FP64 operator and test hooks.
+// Algorithm (a) of Sect. 2 par. 4: direct F_n-transforms along every axis, division by
+// the eigenvalue sums, inverse F_n-transforms; refined dtypes wrap low-precision solves
+// in iterative refinement with the FP64 matrix-free residual.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "residual.cuh"
+#include "sweep.cuh"
+
+using namespace hofem;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+hofem_status fail(hofem_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+hofem_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? HOFEM_ERR_OOM : HOFEM_ERR_CUDA;
+}
+
+#define HOFEM_CUDA(x, where)                       \
+  do {                                             \
+    cudaError_t e__ = (x);                         \
+    if (e__ != cudaSuccess) return cuda_fail(e__, where); \
+  } while (0)
+
+constexpr int kThreads = 512;
+constexpr size_t kSmemLimit = 232448;   // 227 KB opt-in per CTA on sm_103
+constexpr int kSMs = 152;
+
+struct DevAxis {
+  AxisTables h;
+  double *lam64 = nullptr, *mix64 = nullptr, *evec64 = nullptr, *tw64 = nullptr;
+  float *lam32 = nullptr, *mix32 = nullptr, *evec32 = nullptr, *tw32 = nullptr;
+  double *Aloc = nullptr, *Cloc = nullptr;
+  int npass = 0, radix[8] = {0};
+};
+
+}  // namespace
+
+struct hofem_plan_s {
+  int N = 0, n = 0, dtype = 0;
+  int K[3] = {0, 0, 0}, M[3] = {0, 0, 0};
+  double X[3] = {0, 0, 0};
+  double alpha = 0.0;
+  long long total = 0;           // unknowns per right-hand side
+  DevAxis ax[3];
+  // workspace
+  int ws_nrhs = 0;
+  float* work32 = nullptr;       // low-precision work array
+  double* r64 = nullptr;         // residual
+  double* tmp64[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* norms = nullptr;       // 2 per rhs
+  double* h_norms = nullptr;     // pinned mirror
+  int refine_iters = 2;
+  double refine_tol = 0.0;
+  hofem_info info{};
+  size_t table_bytes = 0;
+  // profiling: event pairs recorded around launches, folded into per-kind totals on query
+  bool profiling = false;
+  struct Pending { int kind; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[16] = {0};
+  int prof_n[16] = {0};
+};
+
+namespace {
+
+const char* const kKindNames[] = {"sweep_fwd_f64", "sweep_fsi_f64", "sweep_inv_f64", "sweep_fwd_f32",
+                                  "sweep_fsi_f32", "sweep_inv_f32", "apply_f64"};
+constexpr int kNumKinds = 7;
+
+cudaEvent_t pool_event(hofem_plan_s* p) {
+  if (!p->pool.empty()) {
+    cudaEvent_t e = p->pool.back();
+    p->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch `fn` on stream s, counting it and bracketing it with events when profiling.
+template <typename F>
+cudaError_t timed_launch(hofem_plan_s* p, int kind, cudaStream_t s, F fn) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (p->profiling) {
+    a = pool_event(p);
+    b = pool_event(p);
+    cudaEventRecord(a, s);
+  }
+  cudaError_t e = fn();
+  if (p->profiling) {
+    cudaEventRecord(b, s);
+    p->pending.push_back({kind, a, b});
+  }
+  if (e == cudaSuccess) ++p->info.kernel_launches;
+  return e;
+}
+
+void fold_profile(hofem_plan_s* p) {
+  for (auto& q : p->pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(q.b);
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+      p->prof_ms[q.kind] += ms;
+      p->prof_n[q.kind] += 1;
+    }
+    p->pool.push_back(q.a);
+    p->pool.push_back(q.b);
+  }
+  p->pending.clear();
+}
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+void radix_plan(int K, int* npass, int* radix) {
+  int m = 0;
+  while ((1 << m) < K) ++m;
+  int np = 0;
+  while (m >= 4) { radix[np++] = 16; m -= 4; }
+  if (m > 0) radix[np++] = 1 << m;
+  *npass = np;
+}
+
+template <typename T>
+hofem_status upload(const std::vector<double>& src, T** dst, size_t* bytes) {
+  std::vector<T> tmp(src.size() ? src.size() : 1);
+  for (size_t i = 0; i < src.size(); ++i) tmp[i] = (T)src[i];
+  HOFEM_CUDA(cudaMalloc(dst, tmp.size() * sizeof(T)), "cudaMalloc(tables)");
+  HOFEM_CUDA(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice), "upload tables");
+  *bytes += tmp.size() * sizeof(T);
+  return HOFEM_OK;
+}
+
+void free_axis(DevAxis& a) {
+  cudaFree(a.lam64); cudaFree(a.mix64); cudaFree(a.evec64); cudaFree(a.tw64);
+  cudaFree(a.lam32); cudaFree(a.mix32); cudaFree(a.evec32); cudaFree(a.tw32);
+  cudaFree(a.Aloc); cudaFree(a.Cloc);
+  a = DevAxis{};
+}
+
+void free_workspace(hofem_plan_s* p) {
+  cudaFree(p->work32); p->work32 = nullptr;
+  cudaFree(p->r64); p->r64 = nullptr;
+  for (auto& t : p->tmp64) { cudaFree(t); t = nullptr; }
+  cudaFree(p->norms); p->norms = nullptr;
+  if (p->h_norms) cudaFreeHost(p->h_norms);
+  p->h_norms = nullptr;
+  p->ws_nrhs = 0;
+  p->info.workspace_bytes = 0;
+}
+
+hofem_status reserve(hofem_plan_s* p, int nrhs) {
+  if (nrhs <= p->ws_nrhs) return HOFEM_OK;
+  free_workspace(p);
+  const size_t cnt = (size_t)nrhs * p->total;
+  size_t bytes = 0;
+  const bool low = p->dtype != HOFEM_FP64;
+  if (low) {
+    HOFEM_CUDA(cudaMalloc(&p->work32, cnt * sizeof(float)), "cudaMalloc(work)");
+    bytes += cnt * sizeof(float);
+  }
+  HOFEM_CUDA(cudaMalloc(&p->r64, cnt * sizeof(double)), "cudaMalloc(residual)");
+  bytes += cnt * sizeof(double);
+  const int ntmp = p->N == 2 ? 2 : 4;
+  for (int i = 0; i < ntmp; ++i) {
+    HOFEM_CUDA(cudaMalloc(&p->tmp64[i], cnt * sizeof(double)), "cudaMalloc(operator temporaries)");
+    bytes += cnt * sizeof(double);
+  }
+  HOFEM_CUDA(cudaMalloc(&p->norms, 2 * (size_t)nrhs * sizeof(double)), "cudaMalloc(norms)");
+  HOFEM_CUDA(cudaMallocHost(&p->h_norms, 2 * (size_t)nrhs * sizeof(double)), "cudaMallocHost(norms)");
+  memset(p->h_norms, 0, 2 * (size_t)nrhs * sizeof(double));
+  p->ws_nrhs = nrhs;
+  p->info.workspace_bytes = bytes;
+  return HOFEM_OK;
+}
+
+int num_jobs_host(int W, int n) { return W * ((n - 1) / 2) + (((n & 1) == 0) ? W : (W + 1) / 2); }
+
+// Lines per CTA (W, power of two) and DST jobs per batch (J) for one sweep.
+bool choose_sweep(int M, int n, int K, int tsize, long long lines, bool strided, int* W_out, int* J_out) {
+  const int maxJ = sweep_max_jobs(K, tsize, kThreads);
+  for (int W = 64; W >= 1; W >>= 1) {
+    if (W > 1 && lines / W < 2 * kSMs) continue;   // keep the grid at >= 2 CTAs per SM
+    int J = std::min(maxJ, num_jobs_host(W, n));
+    while (J >= 1 && sweep_smem_bytes(M, n, K, W, J, tsize, strided) > kSmemLimit) --J;
+    if (J < 1) continue;
+    if (W > 1 && J < std::min(W / 2, num_jobs_host(W, n))) continue;
+    *W_out = W;
+    *J_out = J;
+    return true;
+  }
+  return false;
+}
+
+struct Geo {
+  long long outer_per_rhs, inner;
+};
+
+Geo geometry(const hofem_plan_s* p, int axis) {
+  Geo g{1, 1};
+  for (int i = 0; i < axis; ++i) g.outer_per_rhs *= p->M[i];
+  for (int i = axis + 1; i < p->N; ++i) g.inner *= p->M[i];
+  return g;
+}
+
+hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void* in, bool in_f64, void* out,
+                       bool out_f64, bool accumulate, double* norms, long long nrhs, cudaStream_t s,
+                       long long lines_override = -1) {
+  const DevAxis& A = p->ax[axis];
+  SweepParams P{};
+  Geo g = geometry(p, axis);
+  if (lines_override >= 0) g = Geo{lines_override, 1};
+  const int tsize = f64 ? 8 : 4;
+  const bool strided = g.inner > 1;
+  const long long lines = nrhs * g.outer_per_rhs * g.inner;
+  int W = 1, J = 1;
+  if (!choose_sweep(A.h.M, A.h.n, A.h.K, tsize, lines, strided, &W, &J))
+    return fail(HOFEM_ERR_UNSUPPORTED, "no launch configuration fits shared memory for this axis");
+  P.outer = nrhs * g.outer_per_rhs;
+  P.inner = g.inner;
+  P.outer_per_rhs = g.outer_per_rhs;
+  P.tiles_per_outer = strided ? (g.inner + W - 1) / W : (g.outer_per_rhs + W - 1) / W;
+  P.ntiles = (strided ? P.outer : nrhs) * P.tiles_per_outer;
+  P.M = A.h.M;
+  P.n = A.h.n;
+  P.K = A.h.K;
+  P.W = W;
+  P.mode = mode;
+  P.in = in;
+  P.in_f64 = in_f64;
+  P.out = out;
+  P.out_f64 = out_f64;
+  P.accumulate = accumulate;
+  P.norms = norms;
+  P.mix = f64 ? (const void*)A.mix64 : (const void*)A.mix32;
+  P.evec = f64 ? (const void*)A.evec64 : (const void*)A.evec32;
+  P.tw = f64 ? (const void*)A.tw64 : (const void*)A.tw32;
+  P.lam = f64 ? (const void*)A.lam64 : (const void*)A.lam32;
+  P.alpha = p->alpha;
+  if (mode == kFwdScaleInv) {
+    // the fused axis is axis 0; lines are columns c = (q_1, .., q_{N-1})
+    const DevAxis& a1 = p->ax[1];
+    P.lamA = f64 ? (const void*)a1.lam64 : (const void*)a1.lam32;
+    if (p->N == 3) {
+      const DevAxis& a2 = p->ax[2];
+      P.lamB = f64 ? (const void*)a2.lam64 : (const void*)a2.lam32;
+      P.MB = p->M[2];
+    } else {
+      P.lamB = nullptr;
+      P.MB = 1;
+    }
+  }
+  P.npass = A.npass;
+  for (int i = 0; i < 8; ++i) P.radix[i] = A.radix[i];
+  P.jobs_per_batch = J;
+  if (strided) { P.ps = W; P.ws = 1; } else { P.ps = 1; P.ws = A.h.M; }
+  P.tile_elems = A.h.M * W;
+  P.threads = kThreads;
+  P.smem_bytes = sweep_smem_bytes(A.h.M, A.h.n, A.h.K, W, J, tsize, strided);
+  p->info.lines_per_cta[axis] = W;
+  if (P.ntiles <= 0) return HOFEM_OK;
+  const int kind = (f64 ? 0 : 3) + (mode == kFwd ? 0 : mode == kFwdScaleInv ? 1 : 2);
+  cudaError_t e = timed_launch(p, kind, s, [&]() { return f64 ? launch_sweep_f64(P, s) : launch_sweep_f32(P, s); });
+  if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+  return HOFEM_OK;
+}
+
+// One low- or full-precision solve f -> u (algorithm (a)); accumulate: u += solution.
+hofem_status solve_once(hofem_plan_s* p, const double* f, double* u, int nrhs, bool f64, bool accumulate,
+                        double* norms, cudaStream_t s) {
+  hofem_status st;
+  void* work = f64 ? (void*)u : (void*)p->work32;
+  if (f64 && accumulate) return fail(HOFEM_ERR_INVALID_ARG, "internal: FP64 solve cannot accumulate");
+  const int N = p->N;
+  // forward along the contiguous axis, then the strided ones down to axis 1
+  if ((st = run_sweep(p, N - 1, kFwd, f64, f, true, work, f64, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
+  for (int a = N - 2; a >= 1; --a)
+    if ((st = run_sweep(p, a, kFwd, f64, work, f64, work, f64, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
+  if ((st = run_sweep(p, 0, kFwdScaleInv, f64, work, f64, work, f64, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
+  for (int a = 1; a <= N - 2; ++a)
+    if ((st = run_sweep(p, a, kInv, f64, work, f64, work, f64, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
+  return run_sweep(p, N - 1, kInv, f64, work, f64, u, true, accumulate, norms, nrhs, s);
+}
+
+hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double* Q_, double* out1, double* out2,
+                       const double* f, double cA, double cCP, double cCQ, int nrhs, cudaStream_t s) {
+  const DevAxis& A = p->ax[axis];
+  Geo g = geometry(p, axis);
+  const bool strided = g.inner > 1;
+  ApplyParams P{};
+  int W = strided ? 32 : 4;
+  int E = strided ? 16 : 64;
+  while (apply_smem_bytes(A.h.n, W, E, Q_ != nullptr) > kSmemLimit && E > 1) E /= 2;
+  E = std::min(E, A.h.K);
+  P.outer = (long long)nrhs * g.outer_per_rhs;
+  P.inner = g.inner;
+  P.outer_per_rhs = g.outer_per_rhs;
+  P.tiles_per_outer = strided ? (g.inner + W - 1) / W : (g.outer_per_rhs + W - 1) / W;
+  P.seg_per_line = (A.h.K + E - 1) / E;
+  P.ntiles = (strided ? P.outer : nrhs) * P.tiles_per_outer * P.seg_per_line;
+  P.M = A.h.M;
+  P.n = A.h.n;
+  P.K = A.h.K;
+  P.W = W;
+  P.E = E;
+  P.P = P_;
+  P.Q = Q_;
+  P.out1 = out1;
+  P.out2 = out2;
+  P.f = f;
+  P.cA = cA;
+  P.cCP = cCP;
+  P.cCQ = cCQ;
+  P.needPC = (out1 != nullptr) || (cCP != 0.0);
+  P.needPA = cA != 0.0;
+  P.Aloc = A.Aloc;
+  P.Cloc = A.Cloc;
+  P.threads = kThreads;
+  P.smem_bytes = apply_smem_bytes(A.h.n, W, E, Q_ != nullptr);
+  if (P.ntiles <= 0) return HOFEM_OK;
+  cudaError_t e = timed_launch(p, 6, s, [&]() { return launch_apply(P, s); });
+  if (e != cudaSuccess) return cuda_fail(e, "operator launch");
+  return HOFEM_OK;
+}
+
+// out = A u (f == nullptr) or out = f - A u, Eq. bvp glob 2, by one sweep per axis.
+hofem_status operator_apply(hofem_plan_s* p, const double* u, const double* f, double* out, int nrhs,
+                            cudaStream_t s) {
+  hofem_status st = reserve(p, nrhs);
+  if (st != HOFEM_OK) return st;
+  const int N = p->N;
+  double sc[3];
+  for (int i = 0; i < N; ++i) sc[i] = 4.0 * (double)p->K[i] * (double)p->K[i] / (p->X[i] * p->X[i]);
+  double** t = p->tmp64;
+  if (N == 2) {
+    // axis 1: T1 = u xC, T2 = s1 (u xA) + alpha (u xC); axis 0: out = [f -] (s0 T1 xA + T2 xC)
+    if ((st = run_apply(p, 1, u, nullptr, t[0], t[1], nullptr, sc[1], p->alpha, 0.0, nrhs, s)) != HOFEM_OK) return st;
+    return run_apply(p, 0, t[0], t[1], nullptr, out, f, sc[0], 0.0, 1.0, nrhs, s);
+  }
+  // N == 3
+  if ((st = run_apply(p, 2, u, nullptr, t[0], t[1], nullptr, sc[2], p->alpha, 0.0, nrhs, s)) != HOFEM_OK) return st;
+  if ((st = run_apply(p, 1, t[0], t[1], t[2], t[3], nullptr, sc[1], 0.0, 1.0, nrhs, s)) != HOFEM_OK) return st;
+  return run_apply(p, 0, t[2], t[3], nullptr, out, f, sc[0], 0.0, 1.0, nrhs, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hofem_status_string(int s) {
+  switch (s) {
+    case HOFEM_OK: return "HOFEM_OK";
+    case HOFEM_ERR_INVALID_ARG: return "HOFEM_ERR_INVALID_ARG";
+    case HOFEM_ERR_UNSUPPORTED: return "HOFEM_ERR_UNSUPPORTED";
+    case HOFEM_ERR_OOM: return "HOFEM_ERR_OOM";
+    case HOFEM_ERR_CUDA: return "HOFEM_ERR_CUDA";
+    case HOFEM_ERR_NOT_CONVERGED: return "HOFEM_ERR_NOT_CONVERGED";
+    case HOFEM_ERR_TIMEOUT: return "HOFEM_ERR_TIMEOUT";
+    default: return "HOFEM_ERR_UNKNOWN";
+  }
+}
+
+const char* hofem_last_error(void) { return g_last_error.c_str(); }
+
+hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, double alpha, hofem_plan_t* out) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!out) return fail(HOFEM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (N != 2 && N != 3) return fail(HOFEM_ERR_INVALID_ARG, "N must be 2 or 3");
+  if (!K || !X) return fail(HOFEM_ERR_INVALID_ARG, "K or X is NULL");
+  if (n < 1 || n > kMaxN) return fail(HOFEM_ERR_INVALID_ARG, "order n must be in 1..16");
+  if (dtype != HOFEM_FP64 && dtype != HOFEM_FP32 && dtype != HOFEM_FP32_REFINED)
+    return fail(HOFEM_ERR_UNSUPPORTED, "dtype not supported");
+  double lam_bound = 0.0;
+  for (int i = 0; i < N; ++i) {
+    if (K[i] < 2) return fail(HOFEM_ERR_INVALID_ARG, "K must be >= 2");
+    if (!is_pow2(K[i]) || K[i] > kMaxK)
+      return fail(HOFEM_ERR_UNSUPPORTED, "K must be a power of two <= 8192");
+    if (!(X[i] > 0.0) || !std::isfinite(X[i])) return fail(HOFEM_ERR_INVALID_ARG, "X must be positive");
+    lam_bound += M_PI * M_PI / (X[i] * X[i]);
+  }
+  if (!(alpha > -lam_bound) || !std::isfinite(alpha))
+    return fail(HOFEM_ERR_INVALID_ARG, "alpha must exceed -pi^2 sum X_i^-2");
+  static bool limits_set = false;
+  if (!limits_set) {
+    HOFEM_CUDA(sweep_set_smem_limits(), "cudaFuncSetAttribute(sweep)");
+    HOFEM_CUDA(apply_set_smem_limits(), "cudaFuncSetAttribute(apply)");
+    limits_set = true;
+  }
+  hofem_plan_s* p = new hofem_plan_s();
+  p->N = N;
+  p->n = n;
+  p->dtype = dtype;
+  p->alpha = alpha;
+  p->total = 1;
+  for (int i = 0; i < N; ++i) {
+    p->K[i] = K[i];
+    p->X[i] = X[i];
+    p->M[i] = n * K[i] - 1;
+    p->total *= p->M[i];
+  }
+  hofem_status st = HOFEM_OK;
+  for (int i = 0; i < N && st == HOFEM_OK; ++i) {
+    DevAxis& a = p->ax[i];
+    std::string err;
+    int same = -1;
+    for (int j = 0; j < i; ++j)
+      if (K[j] == K[i] && X[j] == X[i]) same = j;
+    if (same >= 0) {
+      a.h = p->ax[same].h;
+    } else {
+      st = build_axis_tables(n, K[i], X[i], &a.h, &err);
+      if (st != HOFEM_OK) { g_last_error = err; break; }
+    }
+    size_t& tb = p->table_bytes;
+    if ((st = upload(a.h.lam, &a.lam64, &tb)) != HOFEM_OK) break;
+    if ((st = upload(a.h.mix, &a.mix64, &tb)) != HOFEM_OK) break;
+    if ((st = upload(a.h.evec, &a.evec64, &tb)) != HOFEM_OK) break;
+    if ((st = upload(a.h.tw, &a.tw64, &tb)) != HOFEM_OK) break;
+    if ((st = upload(a.h.lam, &a.lam32, &tb)) != HOFEM_OK) break;
+    if ((st = upload(a.h.mix, &a.mix32, &tb)) != HOFEM_OK) break;
+    if ((st = upload(a.h.evec, &a.evec32, &tb)) != HOFEM_OK) break;
+    if ((st = upload(a.h.tw, &a.tw32, &tb)) != HOFEM_OK) break;
+    if ((st = upload(a.h.Aloc, &a.Aloc, &tb)) != HOFEM_OK) break;
+    if ((st = upload(a.h.Cloc, &a.Cloc, &tb)) != HOFEM_OK) break;
+    radix_plan(K[i], &a.npass, a.radix);
+  }
+  if (st != HOFEM_OK) {
+    for (int i = 0; i < N; ++i) free_axis(p->ax[i]);
+    delete p;
+    return st;
+  }
+  p->refine_iters = dtype == HOFEM_FP32_REFINED ? 2 : 0;
+  hofem_info& inf = p->info;
+  inf.N = N;
+  inf.n = n;
+  for (int i = 0; i < N; ++i) {
+    inf.K[i] = K[i];
+    inf.M[i] = p->M[i];
+  }
+  inf.dtype = dtype;
+  inf.refine_iters = p->refine_iters;
+  inf.table_bytes = p->table_bytes;
+  inf.threads_per_cta = kThreads;
+  inf.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = p;
+  return HOFEM_OK;
+}
+
+hofem_status hofem_set_refinement(hofem_plan_t p, int iters, double tol) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (p->dtype != HOFEM_FP32_REFINED) return fail(HOFEM_ERR_INVALID_ARG, "plan dtype is not refined");
+  if (iters < 0 || iters > 16 || !(tol >= 0.0)) return fail(HOFEM_ERR_INVALID_ARG, "iters in 0..16, tol >= 0");
+  p->refine_iters = iters;
+  p->refine_tol = tol;
+  p->info.refine_iters = iters;
+  return HOFEM_OK;
+}
+
+hofem_status hofem_reserve(hofem_plan_t p, int nrhs) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "nrhs must be >= 1");
+  return reserve(p, nrhs);
+}
+
+hofem_status hofem_solve(hofem_plan_t p, const double* f, double* u, int nrhs, void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (!f || !u) return fail(HOFEM_ERR_INVALID_ARG, "f or u is NULL");
+  if (nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "nrhs must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool refined = p->dtype == HOFEM_FP32_REFINED;
+  if (refined && (const void*)f == (const void*)u)
+    return fail(HOFEM_ERR_INVALID_ARG, "f and u must differ for refined solves");
+  hofem_status st;
+  if (p->dtype == HOFEM_FP64) {
+    st = solve_once(p, f, u, nrhs, true, false, nullptr, s);
+    p->info.iterations = 0;
+    p->info.converged = 1;
+    return st;
+  }
+  if ((st = reserve(p, nrhs)) != HOFEM_OK) return st;
+  if ((st = solve_once(p, f, u, nrhs, false, false, nullptr, s)) != HOFEM_OK) return st;
+  const int iters = refined ? p->refine_iters : 0;
+  int done = 0;
+  bool converged = false;
+  for (int i = 0; i < iters; ++i) {
+    if ((st = operator_apply(p, u, f, p->r64, nrhs, s)) != HOFEM_OK) return st;
+    HOFEM_CUDA(cudaMemsetAsync(p->norms, 0, 2 * (size_t)nrhs * sizeof(double), s), "memset norms");
+    if ((st = solve_once(p, p->r64, u, nrhs, false, true, p->norms, s)) != HOFEM_OK) return st;
+    ++done;
+    if (p->refine_tol > 0.0) {
+      HOFEM_CUDA(cudaMemcpyAsync(p->h_norms, p->norms, 2 * (size_t)nrhs * sizeof(double), cudaMemcpyDeviceToHost, s),
+                 "copy norms");
+      HOFEM_CUDA(cudaStreamSynchronize(s), "stream sync (refinement tolerance)");
+      double worst = 0.0;
+      for (int r = 0; r < nrhs; ++r) {
+        const double nu = p->h_norms[2 * r + 1];
+        worst = std::max(worst, nu > 0 ? std::sqrt(p->h_norms[2 * r] / nu) : 0.0);
+      }
+      if (worst <= p->refine_tol) { converged = true; break; }
+    }
+  }
+  if (p->refine_tol <= 0.0) {
+    converged = true;   // fixed iteration count
+    if (iters > 0)
+      HOFEM_CUDA(cudaMemcpyAsync(p->h_norms, p->norms, 2 * (size_t)nrhs * sizeof(double), cudaMemcpyDeviceToHost, s),
+                 "copy norms");
+  }
+  p->info.iterations = done;
+  p->info.converged = converged ? 1 : 0;
+  if (refined && p->refine_tol > 0.0 && !converged)
+    return fail(HOFEM_ERR_NOT_CONVERGED, "refinement did not reach the tolerance");
+  return HOFEM_OK;
+}
+
+hofem_status hofem_apply(hofem_plan_t p, const double* u, double* r, int nrhs, void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (!u || !r || nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or nrhs");
+  if ((const void*)u == (const void*)r) return fail(HOFEM_ERR_INVALID_ARG, "u and r must differ");
+  return operator_apply(p, u, nullptr, r, nrhs, (cudaStream_t)stream);
+}
+
+hofem_status hofem_residual(hofem_plan_t p, const double* f, const double* u, double* r, int nrhs, void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (!f || !u || !r || nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or nrhs");
+  if ((const void*)u == (const void*)r) return fail(HOFEM_ERR_INVALID_ARG, "u and r must differ");
+  return operator_apply(p, u, f, r, nrhs, (cudaStream_t)stream);
+}
+
+hofem_status hofem_transform1d(hofem_plan_t p, int axis, int inverse, const double* in, double* out, long lines,
+                               void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (axis < 0 || axis >= p->N) return fail(HOFEM_ERR_INVALID_ARG, "axis out of range");
+  if (!in || !out || lines < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or lines");
+  const bool f64 = p->dtype == HOFEM_FP64;
+  // work in the output buffer: FP64 in place, or via the FP32 path converting on load/store
+  return run_sweep(p, axis, inverse ? kInv : kFwd, f64, in, true, out, true, false, nullptr, 1,
+                   (cudaStream_t)stream, lines);
+}
+
+hofem_status hofem_get_eigen(hofem_plan_t p, int axis, double* lam, double* mix, double* evec) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (axis < 0 || axis >= p->N) return fail(HOFEM_ERR_INVALID_ARG, "axis out of range");
+  const AxisTables& h = p->ax[axis].h;
+  if (lam) memcpy(lam, h.lam.data(), h.lam.size() * sizeof(double));
+  if (mix) memcpy(mix, h.mix.data(), h.mix.size() * sizeof(double));
+  if (evec && h.n > 1) memcpy(evec, h.evec.data(), (size_t)(h.n - 1) * (h.n - 1) * sizeof(double));
+  return HOFEM_OK;
+}
+
+hofem_status hofem_get_info(hofem_plan_t p, hofem_info* out) {
+  if (!p || !out) return fail(HOFEM_ERR_INVALID_ARG, "plan or out is NULL");
+  hofem_info inf = p->info;
+  double worst = 0.0;
+  if (p->h_norms)
+    for (int r = 0; r < p->ws_nrhs; ++r) {
+      const double nu = p->h_norms[2 * r + 1];
+      if (nu > 0) worst = std::max(worst, std::sqrt(p->h_norms[2 * r] / nu));
+    }
+  inf.last_rel_update = worst;
+  *out = inf;
+  return HOFEM_OK;
+}
+
+hofem_status hofem_profile(hofem_plan_t p, int enable) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  fold_profile(p);
+  for (int i = 0; i < 16; ++i) {
+    p->prof_ms[i] = 0.0;
+    p->prof_n[i] = 0;
+  }
+  p->profiling = enable != 0;
+  return HOFEM_OK;
+}
+
+hofem_status hofem_get_profile(hofem_plan_t p, hofem_kernel_time* out, int max_entries, int* count) {
+  if (!p || !count || (max_entries > 0 && !out)) return fail(HOFEM_ERR_INVALID_ARG, "bad arguments");
+  fold_profile(p);
+  int c = 0;
+  for (int k = 0; k < kNumKinds; ++k) {
+    if (p->prof_n[k] == 0) continue;
+    if (c < max_entries) {
+      memset(out[c].name, 0, sizeof out[c].name);
+      strncpy(out[c].name, kKindNames[k], sizeof out[c].name - 1);
+      out[c].launches = p->prof_n[k];
+      out[c].total_ms = p->prof_ms[k];
+    }
+    ++c;
+  }
+  *count = c;
+  return HOFEM_OK;
+}
+
+void hofem_destroy(hofem_plan_t p) {
+  if (!p) return;
+  fold_profile(p);
+  for (auto e : p->pool) cudaEventDestroy(e);
+  p->pool.clear();
+  free_workspace(p);
+  for (int i = 0; i < p->N; ++i) free_axis(p->ax[i]);
+  delete p;
+}
+
+}  // extern "C"

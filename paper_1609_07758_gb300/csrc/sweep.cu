@@ -1,0 +1,622 @@
+// Axis sweep kernel: direct (Theorem 2 part 2) and inverse (Theorem 2 part 1) F_n-
+// transforms of W lines of one axis held in shared memory, optionally fused with the
+// eigenvalue-sum scaling of algorithm (a) (Eq. decomp v 2).
+//
+// Line layout: unknown p = (j-1) n + (i-1) is element j's local point i (i = n: node j).
+// Spectral layout after a direct transform: q = (k-1) n + (l-1) for k = 1..K-1 (the n
+// modes of frequency k), then q = n (K-1) + (l-1) for the k = 0 modes (Theorem 1 part 2).
+//
+// Direct transform of y (Theorem 2 part 2, with the eigenvectors of Theorem 1 part 3
+// normalised by u^T C_k u = 1, so that ||s||_C^2 = K):
+//   nodes      Y_j = y_j,                                j = 1..K-1
+//   interiors  z_{j,i} = y_{j+1/2,i} + y_{j-1/2,n-i},    j = 1..K-1  (the even/odd
+//              combination of the theorem written without splitting into parts)
+//   n DST-I    Yhat_k = sum_j Y_j sin(pi k j / K),  Zhat_{k,i} likewise
+//   mixing     w_{k,l} = (c_l Yhat_k + q_l . Zhat_k) / K
+//   k = 0      w_{0,l} = e^(l) . sum_j (-P)^{j-1} y_{j-1/2} / K
+// Inverse transform (Theorem 2 part 1): a_k = sum_l c_l w_{k,l}, d_k = sum_l q_l w_{k,l},
+// g = sum_l w_{0,l} e^(l); A_j, D_j = DST-I of a, d; v_j = A_j and
+// v_{j-1/2} = D_{j-1} + P D_j + (-P)^{j-1} g with D_0 = D_K = 0.  The paper's
+// [n/2] DST-III + [(n-1)/2] DCT-III of the element-centre values are replaced here by
+// n DST-I of the node-aligned sequences, which is the same linear map.
+//
+// DST-I on the GPU: two real sequences a, b form x = a + i b; the 2K-point DFT of the
+// odd extension of x is -2i (DST(a) + i DST(b)).  One radix-2 decimation-in-frequency
+// step splits it into two K-point complex FFTs of u_j = x_j - x_{K-j} (even outputs)
+// and v_j = (x_j + x_{K-j}) exp(-i pi j / K) (odd outputs), done in shared memory by
+// Stockham autosort passes of radix 2..16 with register butterflies.
+#include <cstdint>
+
+#include "sweep.cuh"
+
+namespace hofem {
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+
+template <typename C> __device__ __forceinline__ C c_add(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C c_sub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C c_mul(C a, C b) {
+  return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+// cos(2 pi k / 16)
+__host__ __device__ constexpr double cos16(int k) {
+  switch (k & 15) {
+    case 0: return 1.0;
+    case 1: return 0.92387953251128675613;
+    case 2: return 0.70710678118654752440;
+    case 3: return 0.38268343236508977173;
+    case 4: return 0.0;
+    case 5: return -0.38268343236508977173;
+    case 6: return -0.70710678118654752440;
+    case 7: return -0.92387953251128675613;
+    case 8: return -1.0;
+    case 9: return -0.92387953251128675613;
+    case 10: return -0.70710678118654752440;
+    case 11: return -0.38268343236508977173;
+    case 12: return 0.0;
+    case 13: return 0.38268343236508977173;
+    case 14: return 0.70710678118654752440;
+    default: return 0.92387953251128675613;
+  }
+}
+
+// b * exp(-2 pi i e / 16) for a compile-time-resolvable e
+template <typename T, typename C> __device__ __forceinline__ C tw16(C b, int e) {
+  e &= 15;
+  if (e == 0) return b;
+  if (e == 4) return C{b.y, -b.x};
+  if (e == 8) return C{-b.x, -b.y};
+  if (e == 12) return C{-b.y, b.x};
+  const T c = (T)cos16(e), s = (T)cos16(e - 4);
+  return C{b.x * c + b.y * s, b.y * c - b.x * s};
+}
+
+template <int R> __host__ __device__ constexpr int bitrev(int i) {
+  int r = 0;
+  for (int b = 1; b < R; b <<= 1) {
+    r = (r << 1) | (i & 1);
+    i >>= 1;
+  }
+  return r;
+}
+
+// In-register forward DFT of R = 2, 4, 8, 16 points (iterative radix-2, natural order out).
+template <typename T, int R, typename C> __device__ __forceinline__ void dft_reg(C (&v)[R]) {
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int j = bitrev<R>(i);
+    if (j > i) {
+      C t = v[i];
+      v[i] = v[j];
+      v[j] = t;
+    }
+  }
+#pragma unroll
+  for (int half = 1; half < R; half <<= 1) {
+#pragma unroll
+    for (int s = 0; s < R; s += 2 * half) {
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        C a = v[s + k];
+        C b = tw16<T>(v[s + k + half], k * (16 / (2 * half)));
+        v[s + k] = c_add(a, b);
+        v[s + k + half] = c_sub(a, b);
+      }
+    }
+  }
+}
+
+template <int R> struct Log2;
+template <> struct Log2<2> { static constexpr int v = 1; };
+template <> struct Log2<4> { static constexpr int v = 2; };
+template <> struct Log2<8> { static constexpr int v = 3; };
+template <> struct Log2<16> { static constexpr int v = 4; };
+
+// Complex registers per thread a pass may hold (R x butterflies per thread).
+template <typename T> struct CReg;
+template <> struct CReg<float> { static constexpr int v = 32; };
+template <> struct CReg<double> { static constexpr int v = 16; };
+
+// One in-place Stockham pass of radix R over nfft FFTs of length N = 2^logN stored
+// back to back in buf; Ns = 2^logNs is the product of the radices already applied.
+// tw[t] = exp(-i pi t / N), t < 2N.
+template <typename T, int R>
+__device__ __forceinline__ void fft_pass(typename Cx<T>::type* buf, int logN, int nfft, int logNs,
+                                         const typename Cx<T>::type* __restrict__ tw) {
+  using C = typename Cx<T>::type;
+  constexpr int LR = Log2<R>::v;
+  constexpr int MAXB = CReg<T>::v / R > 0 ? CReg<T>::v / R : 1;
+  const int N = 1 << logN;
+  const int logB = logN - LR;               // butterflies per FFT = N / R
+  const int nb = nfft << logB;
+  const int Ns = 1 << logNs;
+  const int tsh = logN - logNs - LR + 1;    // exponent step in units of exp(-i pi / N)
+  const int mask2N = 2 * N - 1;
+  C v[MAXB][R];
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = threadIdx.x + i * blockDim.x;
+    if (b < nb) {
+      const int f = b >> logB;
+      const int j = b & ((1 << logB) - 1);
+      const int kk = j & (Ns - 1);
+      C* base = buf + ((size_t)f << logN) + j;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i][r] = base[r << logB];
+      if (kk != 0) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[i][r] = c_mul(v[i][r], tw[((kk * r) << tsh) & mask2N]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = threadIdx.x + i * blockDim.x;
+    if (b < nb) {
+      const int f = b >> logB;
+      const int j = b & ((1 << logB) - 1);
+      const int kk = j & (Ns - 1);
+      dft_reg<T, R>(v[i]);
+      C* base = buf + ((size_t)f << logN) + (((j >> logNs) << (logNs + LR)) + kk);
+#pragma unroll
+      for (int r = 0; r < R; ++r) base[r << logNs] = v[i][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void fft_all(typename Cx<T>::type* buf, int logN, int nfft, const SweepParams& P,
+                        const typename Cx<T>::type* __restrict__ tw) {
+  int logNs = 0;
+  for (int ps = 0; ps < P.npass; ++ps) {
+    const int R = P.radix[ps];
+    if (R == 16) fft_pass<T, 16>(buf, logN, nfft, logNs, tw);
+    else if (R == 8) fft_pass<T, 8>(buf, logN, nfft, logNs, tw);
+    else if (R == 4) fft_pass<T, 4>(buf, logN, nfft, logNs, tw);
+    else fft_pass<T, 2>(buf, logN, nfft, logNs, tw);
+    logNs += (R == 16) ? 4 : (R == 8) ? 3 : (R == 4) ? 2 : 1;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Job = one complex DST pair: real part = component ma of line wa, imaginary part =
+// component mb of line wb (mb < 0: absent).  Component 0 = nodes, i = 1..n-1 interior.
+struct Job {
+  int wa, ma, wb, mb;
+};
+
+__device__ __forceinline__ Job job_of(int jx, int W, int n) {
+  const int P = (n - 1) / 2;   // interior pairs (g, n-g), g = 1..P
+  if (jx < W * P) {
+    const int g = jx / W + 1, w = jx - (g - 1) * W;
+    return Job{w, g, w, n - g};
+  }
+  const int r = jx - W * P;
+  if ((n & 1) == 0) return Job{r, 0, r, n / 2};                 // nodes + middle interior
+  return Job{2 * r, 0, 2 * r + 1 < W ? 2 * r + 1 : -1, 2 * r + 1 < W ? 0 : -1};  // nodes of 2 lines
+}
+
+__host__ __device__ __forceinline__ int num_jobs(int W, int n) {
+  const int P = (n - 1) / 2;
+  return W * P + (((n & 1) == 0) ? W : (W + 1) / 2);
+}
+
+template <typename T> struct Tile {
+  T* t;
+  int ps, ws;
+  __device__ __forceinline__ T& at(int p, int w) const { return t[p * ps + w * ws]; }
+};
+
+// spectral / node-aligned slot of component m inside a frequency block
+__device__ __forceinline__ int slot_of(int m, int n) { return m == 0 ? n - 1 : m - 1; }
+
+// forward pre-combined sequence value of component m of line w at j (1..K-1)
+template <typename T>
+__device__ __forceinline__ T fwd_seq(const Tile<T>& tl, int w, int m, int j, int n) {
+  if (m == 0) return tl.at(j * n - 1, w);
+  return tl.at(j * n + m - 1, w) + tl.at((j - 1) * n + n - m - 1, w);
+}
+
+template <typename T>
+__device__ __forceinline__ typename Cx<T>::type pair_x(const Tile<T>& tl, const Job& jb, int j, int n, int K,
+                                                      bool inverse) {
+  using C = typename Cx<T>::type;
+  if (j <= 0 || j >= K) return C{(T)0, (T)0};
+  T a, b = (T)0;
+  if (!inverse) {
+    a = fwd_seq(tl, jb.wa, jb.ma, j, n);
+    if (jb.mb >= 0) b = fwd_seq(tl, jb.wb, jb.mb, j, n);
+  } else {
+    a = tl.at((j - 1) * n + slot_of(jb.ma, n), jb.wa);
+    if (jb.mb >= 0) b = tl.at((j - 1) * n + slot_of(jb.mb, n), jb.wb);
+  }
+  return C{a, b};
+}
+
+// Fill the FFT buffer for jobs [j0, j0 + nj): u (even outputs) and v (odd outputs).
+template <typename T>
+__device__ void dst_load(const Tile<T>& tl, typename Cx<T>::type* buf, int j0, int nj, int W, int n, int K,
+                         bool inverse, const typename Cx<T>::type* __restrict__ tw) {
+  using C = typename Cx<T>::type;
+  const int half = K / 2;
+  const int items = nj * (half + 1);
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int jb = it % nj, t = it / nj;
+    const Job job = job_of(j0 + jb, W, n);
+    C* U = buf + (size_t)(2 * jb) * K;
+    C* V = U + K;
+    const C x1 = pair_x(tl, job, t, n, K, inverse);
+    const C x2 = pair_x(tl, job, K - t, n, K, inverse);
+    const C d = c_sub(x1, x2), s = c_add(x1, x2);
+    if (t == 0) {
+      U[0] = C{(T)0, (T)0};
+      V[0] = C{(T)0, (T)0};
+    } else if (t == half) {
+      U[t] = C{(T)0, (T)0};
+      V[t] = c_mul(s, tw[t]);
+    } else {
+      U[t] = d;
+      U[K - t] = C{-d.x, -d.y};
+      V[t] = c_mul(s, tw[t]);
+      V[K - t] = c_mul(s, tw[K - t]);
+    }
+  }
+}
+
+// 2 x DST of the real part (first) and imaginary part (second) at index k (1..K-1).
+template <typename T>
+__device__ __forceinline__ void dst_out(const typename Cx<T>::type* buf, int jb, int K, int k, T* a, T* b) {
+  const typename Cx<T>::type* U = buf + (size_t)(2 * jb) * K;
+  const typename Cx<T>::type R = (k & 1) ? U[K + (k >> 1)] : U[k >> 1];
+  *a = -R.y;
+  *b = R.x;
+}
+
+template <typename T>
+__device__ void forward_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf, T* tsave, int W, int n,
+                                  int K, const SweepParams& P, const T* __restrict__ mix,
+                                  const T* __restrict__ evec, const typename Cx<T>::type* __restrict__ tw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  // k = 0 sums t_i = sum_j (-P)^{j-1} y_{j-1/2}, component i
+  for (int item = warp; item < W * (n - 1); item += nwarp) {
+    const int w = item % W, i = item / W + 1;
+    T acc = (T)0;
+    for (int j = 1 + lane; j <= K; j += 32) {
+      const T v = tl.at((j - 1) * n + ((j & 1) ? i : n - i) - 1, w);
+      acc += (j & 1) ? v : -v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) tsave[w * (n - 1) + i - 1] = acc;
+  }
+  __syncthreads();
+  // DST jobs, batch by batch
+  const int logK = 31 - __clz(K);
+  const int nj_tot = num_jobs(W, n), J = P.jobs_per_batch;
+  for (int j0 = 0; j0 < nj_tot; j0 += J) {
+    const int nj = min(J, nj_tot - j0);
+    dst_load<T>(tl, fbuf, j0, nj, W, n, K, false, tw);
+    __syncthreads();
+    fft_all<T>(fbuf, logK, 2 * nj, P, tw + 0);
+    // twiddles of the K-point FFT are tw[2 s]: fft_pass indexes in units of exp(-i pi / K)
+    const int items = nj * (K - 1);
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int jb = it % nj, k = it / nj + 1;
+      const Job job = job_of(j0 + jb, W, n);
+      T a, b;
+      dst_out<T>(fbuf, jb, K, k, &a, &b);
+      tl.at((k - 1) * n + slot_of(job.ma, n), job.wa) = a;
+      if (job.mb >= 0) tl.at((k - 1) * n + slot_of(job.mb, n), job.wb) = b;
+    }
+    __syncthreads();
+  }
+  // k = 0 block
+  for (int it = threadIdx.x; it < W * (n - 1); it += blockDim.x) {
+    const int w = it % W, i = it / W;
+    tl.at((K - 1) * n + i, w) = tsave[w * (n - 1) + i];
+  }
+  __syncthreads();
+  // mixing: w_k = G_k xhat_k / (2K)  (the DST outputs above are 2 x DST)
+  const T sc = (T)(0.5 / K), sc0 = (T)(1.0 / K);
+  for (int it = threadIdx.x; it < W * K; it += blockDim.x) {
+    const int w = it % W, k = it / W;     // k = 0 denotes the k = 0 block
+    T x[kMaxN], y[kMaxN];
+    if (k > 0) {
+      const int base = (k - 1) * n;
+#pragma unroll
+      for (int s = 0; s < kMaxN; ++s)
+        if (s < n) x[s] = tl.at(base + s, w);
+      const T* G = mix + (size_t)(k - 1) * n * n;
+#pragma unroll
+      for (int l = 0; l < kMaxN; ++l) {
+        if (l < n) {
+          T acc = (T)0;
+#pragma unroll
+          for (int s = 0; s < kMaxN; ++s)
+            if (s < n) acc = fma(__ldg(G + l * n + s), x[s], acc);
+          y[l] = acc * sc;
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < kMaxN; ++l)
+        if (l < n) tl.at(base + l, w) = y[l];
+    } else if (n > 1) {
+      const int base = (K - 1) * n, m = n - 1;
+#pragma unroll
+      for (int s = 0; s < kMaxN - 1; ++s)
+        if (s < m) x[s] = tl.at(base + s, w);
+#pragma unroll
+      for (int l = 0; l < kMaxN - 1; ++l) {
+        if (l < m) {
+          T acc = (T)0;
+#pragma unroll
+          for (int s = 0; s < kMaxN - 1; ++s)
+            if (s < m) acc = fma(__ldg(evec + l * m + s), x[s], acc);
+          y[l] = acc * sc0;
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < kMaxN - 1; ++l)
+        if (l < m) tl.at(base + l, w) = y[l];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void inverse_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf, T* gsave, int W, int n,
+                                  int K, const SweepParams& P, const T* __restrict__ mix,
+                                  const T* __restrict__ evec, const typename Cx<T>::type* __restrict__ tw) {
+  // mixing: xhat_k = G_k^T w_k / 2 (the DST below returns 2 x DST); g = E^T w_0
+  for (int it = threadIdx.x; it < W * K; it += blockDim.x) {
+    const int w = it % W, k = it / W;
+    T x[kMaxN], y[kMaxN];
+    if (k > 0) {
+      const int base = (k - 1) * n;
+#pragma unroll
+      for (int l = 0; l < kMaxN; ++l)
+        if (l < n) x[l] = tl.at(base + l, w);
+      const T* G = mix + (size_t)(k - 1) * n * n;
+#pragma unroll
+      for (int s = 0; s < kMaxN; ++s) {
+        if (s < n) {
+          T acc = (T)0;
+#pragma unroll
+          for (int l = 0; l < kMaxN; ++l)
+            if (l < n) acc = fma(__ldg(G + l * n + s), x[l], acc);
+          y[s] = acc * (T)0.5;
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < kMaxN; ++s)
+        if (s < n) tl.at(base + s, w) = y[s];
+    } else if (n > 1) {
+      const int base = (K - 1) * n, m = n - 1;
+#pragma unroll
+      for (int l = 0; l < kMaxN - 1; ++l)
+        if (l < m) x[l] = tl.at(base + l, w);
+#pragma unroll
+      for (int i = 0; i < kMaxN - 1; ++i) {
+        if (i < m) {
+          T acc = (T)0;
+#pragma unroll
+          for (int l = 0; l < kMaxN - 1; ++l)
+            if (l < m) acc = fma(__ldg(evec + l * m + i), x[l], acc);
+          gsave[w * m + i] = acc;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int logK = 31 - __clz(K);
+  const int nj_tot = num_jobs(W, n), J = P.jobs_per_batch;
+  for (int j0 = 0; j0 < nj_tot; j0 += J) {
+    const int nj = min(J, nj_tot - j0);
+    dst_load<T>(tl, fbuf, j0, nj, W, n, K, true, tw);
+    __syncthreads();
+    fft_all<T>(fbuf, logK, 2 * nj, P, tw);
+    // post-combine into physical rows
+    const int items = nj * K;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int jb = it % nj, j = it / nj + 1;   // j = 1..K
+      const Job job = job_of(j0 + jb, W, n);
+      T a0 = (T)0, b0 = (T)0, a1 = (T)0, b1 = (T)0;   // D at j-1 and at j
+      if (j - 1 >= 1) dst_out<T>(fbuf, jb, K, j - 1, &a0, &b0);
+      if (j <= K - 1) dst_out<T>(fbuf, jb, K, j, &a1, &b1);
+      if (job.ma == 0) {                        // nodes of line wa (and maybe wb)
+        if (j <= K - 1) {
+          tl.at(j * n - 1, job.wa) = a1;
+          if (job.mb == 0) tl.at(j * n - 1, job.wb) = b1;
+        }
+        if (job.mb > 0) {                        // middle interior component n/2 (n even)
+          const int i = job.mb, m = n - 1;
+          const T g = gsave[job.wb * m + i - 1];
+          tl.at((j - 1) * n + i - 1, job.wb) = b0 + b1 + ((j & 1) ? g : -g);
+        }
+      } else {                                   // interior pair (i, n-i) of line wa
+        const int i = job.ma, ic = job.mb, m = n - 1, w = job.wa;
+        const T gi = gsave[w * m + i - 1], gic = gsave[w * m + ic - 1];
+        // v_{j-1/2} = D_{j-1} + P D_j + (-P)^{j-1} g
+        const T vi = a0 + b1 + ((j & 1) ? gi : -gic);
+        const T vic = b0 + a1 + ((j & 1) ? gic : -gi);
+        tl.at((j - 1) * n + i - 1, w) = vi;
+        tl.at((j - 1) * n + ic - 1, w) = vic;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T> __device__ __forceinline__ T ldcvt(const void* p, size_t i, int f64) {
+  return f64 ? (T)__ldg((const double*)p + i) : (T)__ldg((const float*)p + i);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
+  using C = typename Cx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = P.M, n = P.n, K = P.K, W = P.W;
+  // shared-memory carve-up
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  size_t off = ((size_t)P.tile_elems * sizeof(T) + 15) & ~(size_t)15;
+  C* fbuf = reinterpret_cast<C*>(smem_raw + off);
+  off += (size_t)P.jobs_per_batch * 2 * K * sizeof(C);
+  T* save = reinterpret_cast<T*>(smem_raw + off);
+  off += ((size_t)W * kMaxN * sizeof(T) + 15) & ~(size_t)15;
+  T* lrest = reinterpret_cast<T*>(smem_raw + off);
+  off += ((size_t)W * sizeof(T) + 15) & ~(size_t)15;
+  double* red = reinterpret_cast<double*>(smem_raw + off);
+
+  const Tile<T> tl{tile, P.ps, P.ws};
+  const bool contiguous = (P.inner == 1);
+  const long long b = blockIdx.x;
+  const long long o = b / P.tiles_per_outer, tix = b - o * P.tiles_per_outer;
+  const long long l0 = tix * W;                     // first line (contiguous) or column (strided)
+  const long long nl = contiguous ? P.outer_per_rhs : P.inner;
+  const int wvalid = (int)min((long long)W, nl - l0);
+  const long long rhs = contiguous ? o : o / P.outer_per_rhs;
+
+  // ---- load
+  if (contiguous) {
+    const size_t base = (size_t)(o * P.outer_per_rhs + l0) * M;
+    for (int w = 0; w < W; ++w)
+      for (int p = threadIdx.x; p < M; p += blockDim.x)
+        tl.at(p, w) = (w < wvalid) ? ldcvt<T>(P.in, base + (size_t)w * M + p, P.in_f64) : (T)0;
+  } else {
+    const size_t base = (size_t)o * M * P.inner + l0;
+    for (int it = threadIdx.x; it < M * W; it += blockDim.x) {
+      const int p = it / W, w = it - p * W;
+      tl.at(p, w) = (w < wvalid) ? ldcvt<T>(P.in, base + (size_t)p * P.inner + w, P.in_f64) : (T)0;
+    }
+  }
+  if (P.mode == kFwdScaleInv) {
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+      const long long c = l0 + w;
+      double lr = P.alpha;
+      if (w < wvalid) {
+        const long long qa = P.lamB ? c / P.MB : c;
+        lr += (double)((const T*)P.lamA)[qa];
+        if (P.lamB) lr += (double)((const T*)P.lamB)[c - qa * P.MB];
+      }
+      lrest[w] = (T)lr;
+    }
+  }
+  __syncthreads();
+
+  const T* mix = (const T*)P.mix;
+  const T* evec = (const T*)P.evec;
+  const C* tw = (const C*)P.tw;
+  if (P.mode & kFwd) forward_transform<T>(tl, fbuf, save, W, n, K, P, mix, evec, tw);
+  if (P.mode == kFwdScaleInv) {
+    const T* lam = (const T*)P.lam;
+    for (int it = threadIdx.x; it < M * W; it += blockDim.x) {
+      const int w = it % W, q = it / W;
+      tl.at(q, w) = tl.at(q, w) / (lam[q] + lrest[w]);
+    }
+    __syncthreads();
+  }
+  if (P.mode & kInv) inverse_transform<T>(tl, fbuf, save, W, n, K, P, mix, evec, tw);
+
+  // ---- store
+  double s_d = 0.0, s_u = 0.0;
+  if (contiguous) {
+    const size_t base = (size_t)(o * P.outer_per_rhs + l0) * M;
+    for (int w = 0; w < wvalid; ++w)
+      for (int p = threadIdx.x; p < M; p += blockDim.x) {
+        const size_t idx = base + (size_t)w * M + p;
+        const T v = tl.at(p, w);
+        if (P.out_f64) {
+          double* out = (double*)P.out;
+          double r = (double)v;
+          if (P.accumulate) r += out[idx];
+          out[idx] = r;
+          s_d += (double)v * (double)v;
+          s_u += r * r;
+        } else {
+          ((float*)P.out)[idx] = (float)v;
+        }
+      }
+  } else {
+    const size_t base = (size_t)o * M * P.inner + l0;
+    for (int it = threadIdx.x; it < M * W; it += blockDim.x) {
+      const int p = it / W, w = it - p * W;
+      if (w >= wvalid) continue;
+      const size_t idx = base + (size_t)p * P.inner + w;
+      const T v = tl.at(p, w);
+      if (P.out_f64) {
+        double* out = (double*)P.out;
+        double r = (double)v;
+        if (P.accumulate) r += out[idx];
+        out[idx] = r;
+        s_d += (double)v * (double)v;
+        s_u += r * r;
+      } else {
+        ((float*)P.out)[idx] = (float)v;
+      }
+    }
+  }
+  if (P.norms) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+      s_d += __shfl_xor_sync(0xffffffffu, s_d, o2);
+      s_u += __shfl_xor_sync(0xffffffffu, s_u, o2);
+    }
+    if (lane == 0) {
+      red[2 * warp] = s_d;
+      red[2 * warp + 1] = s_u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, c = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+        a += red[2 * i];
+        c += red[2 * i + 1];
+      }
+      atomicAdd(&P.norms[2 * rhs], a);
+      atomicAdd(&P.norms[2 * rhs + 1], c);
+    }
+  }
+}
+
+size_t sweep_smem_bytes(int M, int n, int K, int W, int J, int tsize, bool strided) {
+  (void)n;
+  (void)strided;
+  size_t off = ((size_t)M * W * tsize + 15) & ~(size_t)15;
+  off += (size_t)J * 2 * K * 2 * tsize;
+  off += ((size_t)W * kMaxN * tsize + 15) & ~(size_t)15;
+  off += ((size_t)W * tsize + 15) & ~(size_t)15;
+  off += 2 * 32 * sizeof(double);
+  return off;
+}
+
+// Largest jobs per batch with every pass's butterflies fitting the register budget.
+int sweep_max_jobs(int K, int tsize, int threads) {
+  const int creg = tsize == 4 ? CReg<float>::v : CReg<double>::v;
+  const long long cap = (long long)threads * creg;   // >= nfft * K complex values
+  long long J = cap / (2LL * K);
+  return (int)(J < 1 ? 0 : J);
+}
+
+cudaError_t sweep_set_smem_limits() {
+  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sweep_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+}
+
+cudaError_t launch_sweep_f32(const SweepParams& p, cudaStream_t s) {
+  sweep_kernel<float><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_f64(const SweepParams& p, cudaStream_t s) {
+  sweep_kernel<double><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace hofem

@@ -1,0 +1,57 @@
+// Axis sweep: the direct / inverse F_n-transform of Theorem 2 applied to every line of
+// one axis of the tensor-product grid, optionally fused with the eigenvalue-sum scaling
+// of algorithm (a) (Eq. decomp v 2).  Host-side launch parameters.
+#pragma once
+#include "common.cuh"
+
+namespace hofem {
+
+enum SweepMode : int { kFwd = 1, kInv = 2, kFwdScaleInv = 3 };
+
+struct SweepParams {
+  // geometry of the sweep: lines along one axis of a C-order array
+  long long outer;            // slabs before the axis (rhs x dims before)
+  long long inner;            // product of dims after the axis (1 = contiguous lines)
+  long long outer_per_rhs;    // slabs per right-hand side
+  long long tiles_per_outer;  // ceil(inner / W) (strided) or ceil(outer_per_rhs / W) (contiguous)
+  long long ntiles;
+  int M, n, K, W;             // line length, order, elements, lines per CTA
+  int mode;
+  // data
+  const void* in;
+  int in_f64;
+  void* out;
+  int out_f64;
+  int accumulate;             // out (FP64) += result
+  double* norms;              // if non-null: per rhs {sum result^2, sum out_new^2} (atomics)
+  // axis tables, in the work precision T
+  const void* mix;            // (K-1) n n
+  const void* evec;           // (n-1)^2
+  const void* tw;             // 2K complex exp(-i pi t / K)
+  const void* lam;            // M
+  // eigenvalue sums of the other axes for the fused sweep (lines are columns c)
+  const void* lamA;           // lam_rest(c) = lamA[c / MB] + lamB[c % MB] (lamB may be null)
+  const void* lamB;
+  long long MB;
+  double alpha;
+  // FFT plan for length K
+  int npass;
+  int radix[8];
+  int jobs_per_batch;
+  // shared-memory layout (in elements of T)
+  int ps, ws;                 // tile(p, w) = tile[p * ps + w * ws]
+  int tile_elems;
+  int threads;
+  size_t smem_bytes;
+};
+
+// Launch one sweep; T = float or double work precision.
+cudaError_t launch_sweep_f32(const SweepParams& p, cudaStream_t s);
+cudaError_t launch_sweep_f64(const SweepParams& p, cudaStream_t s);
+
+// Shared-memory bytes a sweep needs for (M, n, K, W, J) in precision of size tsize.
+size_t sweep_smem_bytes(int M, int n, int K, int W, int J, int tsize, bool strided);
+int sweep_max_jobs(int K, int tsize, int threads);
+cudaError_t sweep_set_smem_limits();
+
+}  // namespace hofem

@@ -1,0 +1,87 @@
+"""GPU parity at the full workload sizes, in the launch configuration bench.py times.
+
+2D n = 9, K = 1024 (9215^2 unknowns): FP64 and FP32 + FP64-residual refinement against
+the oracle's dense tensor-product solve, rel. L2 <= 1e-12.  2D n = 2, K = 64 with the
+manufactured sine solution plus noise.  3D n = 4, K = 128 (511^3) refined.
+"""
+import numpy as np
+import pytest
+
+from oracle import load as oload
+from oracle import solve as osolve
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_07758_gb300 import build as b
+    b.build()
+
+
+def H():
+    import paper_1609_07758_gb300 as hofem
+    return hofem
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def test_2d_n2_k64_manufactured_with_noise():
+    from paper_1609_07758_gb300 import inputs
+    n, K = 2, 64
+    M = n * K - 1
+    a, b, noise = inputs.manufactured_params(1, (M, M))
+    lapl = np.pi ** 2 * (a * a + b * b)
+    fh = oload.load_vector_separable([(lapl, [lambda x: np.sin(np.pi * a * x), lambda y: np.sin(np.pi * b * y)])],
+                                     [n, n], [K, K], [1.0, 1.0]) + noise
+    ref = osolve.solve_tensor(fh[None], [n, n], [K, K], [1.0, 1.0])[0]
+    for dtype in (H().HOFEM_FP64, H().HOFEM_FP32_REFINED):
+        plan = H().Plan(2, [K, K], n, [1.0, 1.0], dtype)
+        fd = torch.from_numpy(fh[None].copy()).cuda()
+        ud = torch.zeros_like(fd)
+        plan.solve(fd, ud, 1)
+        torch.cuda.synchronize()
+        assert rel_l2(ud.cpu().numpy()[0], ref) <= 1e-12
+    # discretisation error against the manufactured solution (noise 1e-3 kept small)
+    x = oload.grid_points(n, K, 1.0)
+    u = np.outer(np.sin(np.pi * a * x), np.sin(np.pi * b * x))
+    assert np.abs(ref - u).max() < 1e-2
+
+
+def test_2d_n9_k1024_fp64_and_mixed_match_oracle():
+    from paper_1609_07758_gb300 import inputs
+    n, K = 9, 1024
+    f = inputs.smooth_sine_rhs(2, n, K)
+    ref = osolve.solve_tensor(f, [n, n], [K, K], [1.0, 1.0])
+    fd = torch.from_numpy(f).cuda()
+    for dtype in (H().HOFEM_FP64, H().HOFEM_FP32_REFINED):
+        plan = H().Plan(2, [K, K], n, [1.0, 1.0], dtype)
+        ud = torch.zeros_like(fd)
+        plan.solve(fd, ud, 1)
+        torch.cuda.synchronize()
+        err = rel_l2(ud.cpu().numpy(), ref)
+        print(f"dtype {dtype}: rel L2 vs oracle {err:.3e}")
+        assert err <= 1e-12
+        plan.close()
+
+
+def test_3d_n4_k128_mixed_matches_oracle():
+    from paper_1609_07758_gb300 import inputs
+    n, K = 4, 128
+    M = n * K - 1
+    f = inputs.gaussian_rhs(3, (1, M, M, M))
+    ref = osolve.solve_tensor(f, [n] * 3, [K] * 3, [1.0] * 3)
+    fd = torch.from_numpy(f).cuda()
+    plan = H().Plan(3, [K] * 3, n, [1.0] * 3, H().HOFEM_FP32_REFINED)
+    ud = torch.zeros_like(fd)
+    plan.solve(fd, ud, 1)
+    torch.cuda.synchronize()
+    err = rel_l2(ud.cpu().numpy(), ref)
+    print(f"3D rel L2 vs oracle {err:.3e}")
+    assert err <= 1e-12
