@@ -45,6 +45,7 @@ struct DevAxis {
   float *lam32 = nullptr, *mix32 = nullptr, *evec32 = nullptr, *tw32 = nullptr;
   double *Aloc = nullptr, *Cloc = nullptr;
   int npass = 0, radix[8] = {0};
+  int mixNP = 0;
 };
 
 }  // namespace
@@ -191,20 +192,31 @@ hofem_status reserve(hofem_plan_s* p, int nrhs) {
 
 int num_jobs_host(int W, int n) { return W * ((n - 1) / 2) + (((n & 1) == 0) ? W : (W + 1) / 2); }
 
-// Lines per CTA (W, power of two) and DST jobs per batch (J) for one sweep.
+// Lines per CTA (W, power of two) and DST jobs per batch (J) for one sweep: the fewest
+// DST batches (block-wide barrier rounds) per line, then the largest W (more reuse of
+// each mixing-table row), keeping >= 2 CTAs per SM when there are enough lines.
 bool choose_sweep(int M, int n, int K, int tsize, long long lines, bool strided, int* W_out, int* J_out) {
-  const int maxJ = sweep_max_jobs(K, tsize, kThreads);
+  (void)strided;
+  double best = 1e30;
+  int bestW = 0, bestJ = 0;
   for (int W = 64; W >= 1; W >>= 1) {
-    if (W > 1 && lines / W < 2 * kSMs) continue;   // keep the grid at >= 2 CTAs per SM
-    int J = std::min(maxJ, num_jobs_host(W, n));
+    if (W > 1 && lines / W < 2 * kSMs) continue;
+    const int jobs = num_jobs_host(W, n);
+    int J = jobs;
     while (J >= 1 && sweep_smem_bytes(M, n, K, W, J, tsize, strided) > kSmemLimit) --J;
     if (J < 1) continue;
-    if (W > 1 && J < std::min(W / 2, num_jobs_host(W, n))) continue;
-    *W_out = W;
-    *J_out = J;
-    return true;
+    const int batches = (jobs + J - 1) / J;
+    const double score = (double)batches / W;
+    if (score < best - 1e-12) {
+      best = score;
+      bestW = W;
+      bestJ = J;
+    }
   }
-  return false;
+  if (bestW == 0) return false;
+  *W_out = bestW;
+  *J_out = bestJ;
+  return true;
 }
 
 struct Geo {
@@ -248,6 +260,7 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   P.accumulate = accumulate;
   P.norms = norms;
   P.mix = f64 ? (const void*)A.mix64 : (const void*)A.mix32;
+  P.mixNP = A.mixNP;
   P.evec = f64 ? (const void*)A.evec64 : (const void*)A.evec32;
   P.tw = f64 ? (const void*)A.tw64 : (const void*)A.tw32;
   P.lam = f64 ? (const void*)A.lam64 : (const void*)A.lam32;
@@ -266,11 +279,14 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
     }
   }
   P.npass = A.npass;
-  for (int i = 0; i < 8; ++i) P.radix[i] = A.radix[i];
+  for (int i = 0; i < 8; ++i) {
+    P.radix[i] = A.radix[i];
+    P.radix_log[i] = A.radix[i] > 0 ? 31 - __builtin_clz(A.radix[i]) : 0;
+  }
   P.jobs_per_batch = J;
   if (strided) { P.ps = W; P.ws = 1; } else { P.ps = 1; P.ws = A.h.M; }
-  P.tile_elems = A.h.M * W;
-  P.threads = kThreads;
+  P.tile_elems = sweep_tile_elems(A.h.M, W, tsize);
+  P.threads = f64 ? 512 : HOFEM_F32_THREADS;
   P.smem_bytes = sweep_smem_bytes(A.h.M, A.h.n, A.h.K, W, J, tsize, strided);
   p->info.lines_per_cta[axis] = W;
   if (P.ntiles <= 0) return HOFEM_OK;
@@ -429,11 +445,19 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
     }
     size_t& tb = p->table_bytes;
     if ((st = upload(a.h.lam, &a.lam64, &tb)) != HOFEM_OK) break;
-    if ((st = upload(a.h.mix, &a.mix64, &tb)) != HOFEM_OK) break;
+    {
+      // mixing rows padded to a multiple of 4 entries for 16-byte vector loads
+      const int np = (n + 3) & ~3;
+      std::vector<double> padded((size_t)(K[i] - 1) * n * np, 0.0);
+      for (size_t r = 0; r < (size_t)(K[i] - 1) * n; ++r)
+        for (int c = 0; c < n; ++c) padded[r * np + c] = a.h.mix[r * n + c];
+      a.mixNP = np;
+      if ((st = upload(padded, &a.mix64, &tb)) != HOFEM_OK) break;
+      if ((st = upload(padded, &a.mix32, &tb)) != HOFEM_OK) break;
+    }
     if ((st = upload(a.h.evec, &a.evec64, &tb)) != HOFEM_OK) break;
     if ((st = upload(a.h.tw, &a.tw64, &tb)) != HOFEM_OK) break;
     if ((st = upload(a.h.lam, &a.lam32, &tb)) != HOFEM_OK) break;
-    if ((st = upload(a.h.mix, &a.mix32, &tb)) != HOFEM_OK) break;
     if ((st = upload(a.h.evec, &a.evec32, &tb)) != HOFEM_OK) break;
     if ((st = upload(a.h.tw, &a.tw32, &tb)) != HOFEM_OK) break;
     if ((st = upload(a.h.Aloc, &a.Aloc, &tb)) != HOFEM_OK) break;

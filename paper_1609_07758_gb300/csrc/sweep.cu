@@ -120,51 +120,60 @@ template <typename T> struct CReg;
 template <> struct CReg<float> { static constexpr int v = 32; };
 template <> struct CReg<double> { static constexpr int v = 16; };
 
-// One in-place Stockham pass of radix R over nfft FFTs of length N = 2^logN stored
-// back to back in buf; Ns = 2^logNs is the product of the radices already applied.
+// Bank-conflict-free layouts.  Tile element e is stored at e + (e >> TileSwz<T>): one pad
+// word per 32 banks' worth, so the stride-n and stride-nW walks of the pre-combine, the
+// post-combine and the mixing hit distinct banks.  FFT buffer entry e of an FFT is stored
+// at e + (e >> FftPad<T>) (one pad complex per 128 bytes), which removes the stride-R
+// conflicts of the first Stockham pass.
+template <typename T> struct TileSwz;
+template <> struct TileSwz<float> { static constexpr int v = 5; };
+template <> struct TileSwz<double> { static constexpr int v = 4; };
+template <typename T> struct FftPad;
+template <> struct FftPad<float> { static constexpr int v = 4; };
+template <> struct FftPad<double> { static constexpr int v = 3; };
+
+template <typename T> __host__ __device__ __forceinline__ int fft_stride(int N) {
+  return N + (N >> FftPad<T>::v);
+}
+template <typename T> __device__ __forceinline__ int fpad(int e) { return e + (e >> FftPad<T>::v); }
+
+// One in-place decimation-in-frequency pass (Gentleman-Sande) of radix R over nfft FFTs
+// of length N = 2^logN stored back to back (padded) in buf.  Blocks have length
+// L = 2^logL; butterfly (block, j) combines the R entries j + r L/R of its block,
+// y_q = sum_r x_r exp(-2 pi i r q / R), then twiddles y_q by exp(-2 pi i j q / L) and
+// stores it back in the slot of x_q.  Every butterfly reads and writes the same R
+// slots, so a pass needs one barrier and one butterfly's registers per thread.  After
+// all passes the output is in mixed-radix digit-reversed order (see fft_pos).
 // tw[t] = exp(-i pi t / N), t < 2N.
 template <typename T, int R>
-__device__ __forceinline__ void fft_pass(typename Cx<T>::type* buf, int logN, int nfft, int logNs,
-                                         const typename Cx<T>::type* __restrict__ tw) {
+__device__ __noinline__ void fft_pass(typename Cx<T>::type* buf, int logN, int nfft, int logL,
+                                      const typename Cx<T>::type* __restrict__ tw) {
   using C = typename Cx<T>::type;
   constexpr int LR = Log2<R>::v;
-  constexpr int MAXB = CReg<T>::v / R > 0 ? CReg<T>::v / R : 1;
   const int N = 1 << logN;
-  const int logB = logN - LR;               // butterflies per FFT = N / R
+  const int logQ = logL - LR;                  // stride L / R
+  const int logB = logN - LR;                  // butterflies per FFT
   const int nb = nfft << logB;
-  const int Ns = 1 << logNs;
-  const int tsh = logN - logNs - LR + 1;    // exponent step in units of exp(-i pi / N)
+  const int FS = fft_stride<T>(N);
+  const int tsh = logN - logL + 1;             // exp(-2 pi i j q / L) = tw[(j q) << tsh]
   const int mask2N = 2 * N - 1;
-  C v[MAXB][R];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const int f = b >> logB;
+    const int rem = b & ((1 << logB) - 1);
+    const int blk = rem >> logQ;
+    const int j = rem & ((1 << logQ) - 1);
+    C* base = buf + (size_t)f * FS;
+    const int e0 = (blk << logL) + j;
+    C v[R];
 #pragma unroll
-  for (int i = 0; i < MAXB; ++i) {
-    const int b = threadIdx.x + i * blockDim.x;
-    if (b < nb) {
-      const int f = b >> logB;
-      const int j = b & ((1 << logB) - 1);
-      const int kk = j & (Ns - 1);
-      C* base = buf + ((size_t)f << logN) + j;
+    for (int r = 0; r < R; ++r) v[r] = base[fpad<T>(e0 + (r << logQ))];
+    dft_reg<T, R>(v);
+    if (j != 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = base[r << logB];
-      if (kk != 0) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[i][r] = c_mul(v[i][r], tw[((kk * r) << tsh) & mask2N]);
-      }
+      for (int q = 1; q < R; ++q) v[q] = c_mul(v[q], tw[((j * q) << tsh) & mask2N]);
     }
-  }
-  __syncthreads();
 #pragma unroll
-  for (int i = 0; i < MAXB; ++i) {
-    const int b = threadIdx.x + i * blockDim.x;
-    if (b < nb) {
-      const int f = b >> logB;
-      const int j = b & ((1 << logB) - 1);
-      const int kk = j & (Ns - 1);
-      dft_reg<T, R>(v[i]);
-      C* base = buf + ((size_t)f << logN) + (((j >> logNs) << (logNs + LR)) + kk);
-#pragma unroll
-      for (int r = 0; r < R; ++r) base[r << logNs] = v[i][r];
-    }
+    for (int q = 0; q < R; ++q) base[fpad<T>(e0 + (q << logQ))] = v[q];
   }
   __syncthreads();
 }
@@ -172,15 +181,28 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::type* buf, int logN, in
 template <typename T>
 __device__ void fft_all(typename Cx<T>::type* buf, int logN, int nfft, const SweepParams& P,
                         const typename Cx<T>::type* __restrict__ tw) {
-  int logNs = 0;
+  int logL = logN;
   for (int ps = 0; ps < P.npass; ++ps) {
     const int R = P.radix[ps];
-    if (R == 16) fft_pass<T, 16>(buf, logN, nfft, logNs, tw);
-    else if (R == 8) fft_pass<T, 8>(buf, logN, nfft, logNs, tw);
-    else if (R == 4) fft_pass<T, 4>(buf, logN, nfft, logNs, tw);
-    else fft_pass<T, 2>(buf, logN, nfft, logNs, tw);
-    logNs += (R == 16) ? 4 : (R == 8) ? 3 : (R == 4) ? 2 : 1;
+    if (R == 16) fft_pass<T, 16>(buf, logN, nfft, logL, tw);
+    else if (R == 8) fft_pass<T, 8>(buf, logN, nfft, logL, tw);
+    else if (R == 4) fft_pass<T, 4>(buf, logN, nfft, logL, tw);
+    else fft_pass<T, 2>(buf, logN, nfft, logL, tw);
+    logL -= (R == 16) ? 4 : (R == 8) ? 3 : (R == 4) ? 2 : 1;
   }
+}
+
+// Memory slot of frequency m after the DIF passes: the low digit of m (base R_1) selects
+// the slot's top digit, and so on.
+__device__ __forceinline__ int fft_pos(int m, int logN, const SweepParams& P) {
+  int pos = 0, sh = logN;
+  for (int ps = 0; ps < P.npass; ++ps) {
+    const int lb = P.radix_log[ps];
+    sh -= lb;
+    pos |= (m & ((1 << lb) - 1)) << sh;
+    m >>= lb;
+  }
+  return pos;
 }
 
 // ---------------------------------------------------------------------------------
@@ -190,13 +212,13 @@ struct Job {
   int wa, ma, wb, mb;
 };
 
-__device__ __forceinline__ Job job_of(int jx, int W, int n) {
-  const int P = (n - 1) / 2;   // interior pairs (g, n-g), g = 1..P
-  if (jx < W * P) {
-    const int g = jx / W + 1, w = jx - (g - 1) * W;
+__device__ __forceinline__ Job job_of(int jx, int W, int logW, int n) {
+  const int P = (n - 1) >> 1;  // interior pairs (g, n-g), g = 1..P
+  if (jx < (P << logW)) {
+    const int g = (jx >> logW) + 1, w = jx & (W - 1);
     return Job{w, g, w, n - g};
   }
-  const int r = jx - W * P;
+  const int r = jx - (P << logW);
   if ((n & 1) == 0) return Job{r, 0, r, n / 2};                 // nodes + middle interior
   return Job{2 * r, 0, 2 * r + 1 < W ? 2 * r + 1 : -1, 2 * r + 1 < W ? 0 : -1};  // nodes of 2 lines
 }
@@ -209,7 +231,10 @@ __host__ __device__ __forceinline__ int num_jobs(int W, int n) {
 template <typename T> struct Tile {
   T* t;
   int ps, ws;
-  __device__ __forceinline__ T& at(int p, int w) const { return t[p * ps + w * ws]; }
+  __device__ __forceinline__ T& at(int p, int w) const {
+    const int e = p * ps + w * ws;
+    return t[e + (e >> TileSwz<T>::v)];
+  }
 };
 
 // spectral / node-aligned slot of component m inside a frequency block
@@ -240,41 +265,157 @@ __device__ __forceinline__ typename Cx<T>::type pair_x(const Tile<T>& tl, const 
 
 // Fill the FFT buffer for jobs [j0, j0 + nj): u (even outputs) and v (odd outputs).
 template <typename T>
-__device__ void dst_load(const Tile<T>& tl, typename Cx<T>::type* buf, int j0, int nj, int W, int n, int K,
-                         bool inverse, const typename Cx<T>::type* __restrict__ tw) {
+__device__ __noinline__ void dst_load(const Tile<T> tl, typename Cx<T>::type* buf, int j0, int nj, int W, int n,
+                                      int K, bool inverse, const typename Cx<T>::type* __restrict__ tw) {
   using C = typename Cx<T>::type;
-  const int half = K / 2;
-  const int items = nj * (half + 1);
+  const int half = K >> 1;
+  const int logH = 30 - __clz(K);           // log2(K / 2)
+  const int logW = 31 - __clz(W);
+  const int items = nj << logH;
+  const int FS = fft_stride<T>(K);
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int jb = it % nj, t = it / nj;
-    const Job job = job_of(j0 + jb, W, n);
-    C* U = buf + (size_t)(2 * jb) * K;
-    C* V = U + K;
-    const C x1 = pair_x(tl, job, t, n, K, inverse);
-    const C x2 = pair_x(tl, job, K - t, n, K, inverse);
-    const C d = c_sub(x1, x2), s = c_add(x1, x2);
+    const int jb = it >> logH, t = it & (half - 1);
+    const Job job = job_of(j0 + jb, W, logW, n);
+    C* U = buf + (size_t)(2 * jb) * FS;
+    C* V = U + FS;
     if (t == 0) {
       U[0] = C{(T)0, (T)0};
       V[0] = C{(T)0, (T)0};
-    } else if (t == half) {
-      U[t] = C{(T)0, (T)0};
-      V[t] = c_mul(s, tw[t]);
-    } else {
-      U[t] = d;
-      U[K - t] = C{-d.x, -d.y};
-      V[t] = c_mul(s, tw[t]);
-      V[K - t] = c_mul(s, tw[K - t]);
+      const C xh = pair_x(tl, job, half, n, K, inverse);      // t = K/2: u = 0, v = 2 x w^{K/2}
+      U[fpad<T>(half)] = C{(T)0, (T)0};
+      V[fpad<T>(half)] = c_mul(c_add(xh, xh), tw[half]);
+      continue;
     }
+    const C x1 = pair_x(tl, job, t, n, K, inverse);
+    const C x2 = pair_x(tl, job, K - t, n, K, inverse);
+    const C d = c_sub(x1, x2), sm = c_add(x1, x2);
+    U[fpad<T>(t)] = d;
+    U[fpad<T>(K - t)] = C{-d.x, -d.y};
+    V[fpad<T>(t)] = c_mul(sm, tw[t]);
+    V[fpad<T>(K - t)] = c_mul(sm, tw[K - t]);
   }
 }
 
 // 2 x DST of the real part (first) and imaginary part (second) at index k (1..K-1).
 template <typename T>
-__device__ __forceinline__ void dst_out(const typename Cx<T>::type* buf, int jb, int K, int k, T* a, T* b) {
-  const typename Cx<T>::type* U = buf + (size_t)(2 * jb) * K;
-  const typename Cx<T>::type R = (k & 1) ? U[K + (k >> 1)] : U[k >> 1];
+__device__ __forceinline__ void dst_out(const typename Cx<T>::type* buf, int jb, int K, int logK, int k, T* a,
+                                        T* b, const SweepParams& P) {
+  const int FS = fft_stride<T>(K);
+  const typename Cx<T>::type* U = buf + (size_t)(2 * jb) * FS;
+  const int pos = fpad<T>(fft_pos(k >> 1, logK, P));
+  const typename Cx<T>::type R = (k & 1) ? U[FS + pos] : U[pos];
   *a = -R.y;
   *b = R.x;
+}
+
+// ---------------------------------------------------------------------------------
+// Per-frequency n x n mixing, one thread per frequency k looping over the tile's lines
+// two at a time; row l of G_k = (q_1..q_{n-1}, c) of mode (k, l) is read with 16-byte
+// vector loads from a table whose rows are padded to NP (a multiple of 4) entries.
+template <typename T, int N>
+__device__ __forceinline__ void load_row(const T* __restrict__ row, T (&g)[N]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int s = 0; s < N; s += 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(row) + s / 4);
+      g[s] = v.x;
+      if (s + 1 < N) g[s + 1] = v.y;
+      if (s + 2 < N) g[s + 2] = v.z;
+      if (s + 3 < N) g[s + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < N; s += 2) {
+      const double2 v = __ldg(reinterpret_cast<const double2*>(row) + s / 2);
+      g[s] = v.x;
+      if (s + 1 < N) g[s + 1] = v.y;
+    }
+  }
+}
+
+template <typename T, int N, bool FWD>
+__device__ __noinline__ void mix_impl(const Tile<T> tl, int W, int K, const T* __restrict__ mix, int NP,
+                         const T* __restrict__ evec, T* save, T scale, T scale0) {
+  constexpr int LC = 2;
+  for (int k = 1 + threadIdx.x; k < K; k += blockDim.x) {
+    const T* Gk = mix + (size_t)(k - 1) * N * NP;
+    const int base = (k - 1) * N;
+    for (int w0 = 0; w0 < W; w0 += LC) {
+      T x[LC][N], y[LC][N];
+#pragma unroll
+      for (int c = 0; c < LC; ++c)
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+          x[c][s] = (w0 + c < W) ? tl.at(base + s, w0 + c) : (T)0;
+          y[c][s] = (T)0;
+        }
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        T g[N];
+        load_row<T, N>(Gk + l * NP, g);
+        if (FWD) {
+#pragma unroll
+          for (int c = 0; c < LC; ++c) {
+            T acc = (T)0;
+#pragma unroll
+            for (int s = 0; s < N; ++s) acc = fma(g[s], x[c][s], acc);
+            y[c][l] = acc * scale;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < LC; ++c)
+#pragma unroll
+            for (int s = 0; s < N; ++s) y[c][s] = fma(g[s], x[c][l], y[c][s]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < LC; ++c)
+        if (w0 + c < W)
+#pragma unroll
+          for (int s = 0; s < N; ++s) tl.at(base + s, w0 + c) = FWD ? y[c][s] : y[c][s] * scale;
+    }
+  }
+  // k = 0 block: w_0 = E t / K (forward, t in the tile) or g = E^T w_0 (inverse, into save)
+  if constexpr (N > 1) {
+    constexpr int Mm = N - 1;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+      const int base = (K - 1) * N;
+      T x[Mm], y[Mm];
+#pragma unroll
+      for (int s = 0; s < Mm; ++s) {
+        x[s] = tl.at(base + s, w);
+        y[s] = (T)0;
+      }
+#pragma unroll
+      for (int l = 0; l < Mm; ++l)
+#pragma unroll
+        for (int s = 0; s < Mm; ++s) {
+          const T e = __ldg(evec + l * Mm + s);
+          if (FWD) y[l] = fma(e, x[s], y[l]);
+          else y[s] = fma(e, x[l], y[s]);
+        }
+#pragma unroll
+      for (int s = 0; s < Mm; ++s) {
+        if (FWD) tl.at(base + s, w) = y[s] * scale0;
+        else save[w * Mm + s] = y[s];
+      }
+    }
+  }
+}
+
+template <typename T, bool FWD>
+__device__ __forceinline__ void mix_dispatch(const Tile<T> tl, int W, int n, int K, const T* __restrict__ mix, int NP,
+                             const T* __restrict__ evec, T* save, T scale, T scale0) {
+  switch (n) {
+#define HOFEM_MIX_CASE(NN) \
+  case NN: mix_impl<T, NN, FWD>(tl, W, K, mix, NP, evec, save, scale, scale0); break;
+    HOFEM_MIX_CASE(1) HOFEM_MIX_CASE(2) HOFEM_MIX_CASE(3) HOFEM_MIX_CASE(4)
+    HOFEM_MIX_CASE(5) HOFEM_MIX_CASE(6) HOFEM_MIX_CASE(7) HOFEM_MIX_CASE(8)
+    HOFEM_MIX_CASE(9) HOFEM_MIX_CASE(10) HOFEM_MIX_CASE(11) HOFEM_MIX_CASE(12)
+    HOFEM_MIX_CASE(13) HOFEM_MIX_CASE(14) HOFEM_MIX_CASE(15) HOFEM_MIX_CASE(16)
+#undef HOFEM_MIX_CASE
+    default: break;
+  }
 }
 
 template <typename T>
@@ -283,8 +424,9 @@ __device__ void forward_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
                                   const T* __restrict__ evec, const typename Cx<T>::type* __restrict__ tw) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   // k = 0 sums t_i = sum_j (-P)^{j-1} y_{j-1/2}, component i
+  const int logW = 31 - __clz(W);
   for (int item = warp; item < W * (n - 1); item += nwarp) {
-    const int w = item % W, i = item / W + 1;
+    const int w = item & (W - 1), i = (item >> logW) + 1;
     T acc = (T)0;
     for (int j = 1 + lane; j <= K; j += 32) {
       const T v = tl.at((j - 1) * n + ((j & 1) ? i : n - i) - 1, w);
@@ -302,14 +444,14 @@ __device__ void forward_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
     const int nj = min(J, nj_tot - j0);
     dst_load<T>(tl, fbuf, j0, nj, W, n, K, false, tw);
     __syncthreads();
-    fft_all<T>(fbuf, logK, 2 * nj, P, tw + 0);
-    // twiddles of the K-point FFT are tw[2 s]: fft_pass indexes in units of exp(-i pi / K)
-    const int items = nj * (K - 1);
+    fft_all<T>(fbuf, logK, 2 * nj, P, tw);
+    const int items = nj << logK;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-      const int jb = it % nj, k = it / nj + 1;
-      const Job job = job_of(j0 + jb, W, n);
+      const int jb = it >> logK, k = it & (K - 1);
+      if (k == 0) continue;
+      const Job job = job_of(j0 + jb, W, logW, n);
       T a, b;
-      dst_out<T>(fbuf, jb, K, k, &a, &b);
+      dst_out<T>(fbuf, jb, K, logK, k, &a, &b, P);
       tl.at((k - 1) * n + slot_of(job.ma, n), job.wa) = a;
       if (job.mb >= 0) tl.at((k - 1) * n + slot_of(job.mb, n), job.wb) = b;
     }
@@ -317,54 +459,12 @@ __device__ void forward_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
   }
   // k = 0 block
   for (int it = threadIdx.x; it < W * (n - 1); it += blockDim.x) {
-    const int w = it % W, i = it / W;
+    const int w = it & (W - 1), i = it >> logW;
     tl.at((K - 1) * n + i, w) = tsave[w * (n - 1) + i];
   }
   __syncthreads();
   // mixing: w_k = G_k xhat_k / (2K)  (the DST outputs above are 2 x DST)
-  const T sc = (T)(0.5 / K), sc0 = (T)(1.0 / K);
-  for (int it = threadIdx.x; it < W * K; it += blockDim.x) {
-    const int w = it % W, k = it / W;     // k = 0 denotes the k = 0 block
-    T x[kMaxN], y[kMaxN];
-    if (k > 0) {
-      const int base = (k - 1) * n;
-#pragma unroll
-      for (int s = 0; s < kMaxN; ++s)
-        if (s < n) x[s] = tl.at(base + s, w);
-      const T* G = mix + (size_t)(k - 1) * n * n;
-#pragma unroll
-      for (int l = 0; l < kMaxN; ++l) {
-        if (l < n) {
-          T acc = (T)0;
-#pragma unroll
-          for (int s = 0; s < kMaxN; ++s)
-            if (s < n) acc = fma(__ldg(G + l * n + s), x[s], acc);
-          y[l] = acc * sc;
-        }
-      }
-#pragma unroll
-      for (int l = 0; l < kMaxN; ++l)
-        if (l < n) tl.at(base + l, w) = y[l];
-    } else if (n > 1) {
-      const int base = (K - 1) * n, m = n - 1;
-#pragma unroll
-      for (int s = 0; s < kMaxN - 1; ++s)
-        if (s < m) x[s] = tl.at(base + s, w);
-#pragma unroll
-      for (int l = 0; l < kMaxN - 1; ++l) {
-        if (l < m) {
-          T acc = (T)0;
-#pragma unroll
-          for (int s = 0; s < kMaxN - 1; ++s)
-            if (s < m) acc = fma(__ldg(evec + l * m + s), x[s], acc);
-          y[l] = acc * sc0;
-        }
-      }
-#pragma unroll
-      for (int l = 0; l < kMaxN - 1; ++l)
-        if (l < m) tl.at(base + l, w) = y[l];
-    }
-  }
+  mix_dispatch<T, true>(tl, W, n, K, mix, P.mixNP, evec, tsave, (T)(0.5 / K), (T)(1.0 / K));
   __syncthreads();
 }
 
@@ -373,47 +473,10 @@ __device__ void inverse_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
                                   int K, const SweepParams& P, const T* __restrict__ mix,
                                   const T* __restrict__ evec, const typename Cx<T>::type* __restrict__ tw) {
   // mixing: xhat_k = G_k^T w_k / 2 (the DST below returns 2 x DST); g = E^T w_0
-  for (int it = threadIdx.x; it < W * K; it += blockDim.x) {
-    const int w = it % W, k = it / W;
-    T x[kMaxN], y[kMaxN];
-    if (k > 0) {
-      const int base = (k - 1) * n;
-#pragma unroll
-      for (int l = 0; l < kMaxN; ++l)
-        if (l < n) x[l] = tl.at(base + l, w);
-      const T* G = mix + (size_t)(k - 1) * n * n;
-#pragma unroll
-      for (int s = 0; s < kMaxN; ++s) {
-        if (s < n) {
-          T acc = (T)0;
-#pragma unroll
-          for (int l = 0; l < kMaxN; ++l)
-            if (l < n) acc = fma(__ldg(G + l * n + s), x[l], acc);
-          y[s] = acc * (T)0.5;
-        }
-      }
-#pragma unroll
-      for (int s = 0; s < kMaxN; ++s)
-        if (s < n) tl.at(base + s, w) = y[s];
-    } else if (n > 1) {
-      const int base = (K - 1) * n, m = n - 1;
-#pragma unroll
-      for (int l = 0; l < kMaxN - 1; ++l)
-        if (l < m) x[l] = tl.at(base + l, w);
-#pragma unroll
-      for (int i = 0; i < kMaxN - 1; ++i) {
-        if (i < m) {
-          T acc = (T)0;
-#pragma unroll
-          for (int l = 0; l < kMaxN - 1; ++l)
-            if (l < m) acc = fma(__ldg(evec + l * m + i), x[l], acc);
-          gsave[w * m + i] = acc;
-        }
-      }
-    }
-  }
+  mix_dispatch<T, false>(tl, W, n, K, mix, P.mixNP, evec, gsave, (T)0.5, (T)1.0);
   __syncthreads();
   const int logK = 31 - __clz(K);
+  const int logW = 31 - __clz(W);
   const int nj_tot = num_jobs(W, n), J = P.jobs_per_batch;
   for (int j0 = 0; j0 < nj_tot; j0 += J) {
     const int nj = min(J, nj_tot - j0);
@@ -421,13 +484,13 @@ __device__ void inverse_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
     __syncthreads();
     fft_all<T>(fbuf, logK, 2 * nj, P, tw);
     // post-combine into physical rows
-    const int items = nj * K;
+    const int items = nj << logK;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-      const int jb = it % nj, j = it / nj + 1;   // j = 1..K
-      const Job job = job_of(j0 + jb, W, n);
+      const int jb = it >> logK, j = (it & (K - 1)) + 1;   // j = 1..K
+      const Job job = job_of(j0 + jb, W, logW, n);
       T a0 = (T)0, b0 = (T)0, a1 = (T)0, b1 = (T)0;   // D at j-1 and at j
-      if (j - 1 >= 1) dst_out<T>(fbuf, jb, K, j - 1, &a0, &b0);
-      if (j <= K - 1) dst_out<T>(fbuf, jb, K, j, &a1, &b1);
+      if (j - 1 >= 1) dst_out<T>(fbuf, jb, K, logK, j - 1, &a0, &b0, P);
+      if (j <= K - 1) dst_out<T>(fbuf, jb, K, logK, j, &a1, &b1, P);
       if (job.ma == 0) {                        // nodes of line wa (and maybe wb)
         if (j <= K - 1) {
           tl.at(j * n - 1, job.wa) = a1;
@@ -457,7 +520,7 @@ template <typename T> __device__ __forceinline__ T ldcvt(const void* p, size_t i
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
+__global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) sweep_kernel(const SweepParams P) {
   using C = typename Cx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = P.M, n = P.n, K = P.K, W = P.W;
@@ -465,7 +528,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   T* tile = reinterpret_cast<T*>(smem_raw);
   size_t off = ((size_t)P.tile_elems * sizeof(T) + 15) & ~(size_t)15;
   C* fbuf = reinterpret_cast<C*>(smem_raw + off);
-  off += (size_t)P.jobs_per_batch * 2 * K * sizeof(C);
+  off += (size_t)P.jobs_per_batch * 2 * fft_stride<T>(K) * sizeof(C);
   T* save = reinterpret_cast<T*>(smem_raw + off);
   off += ((size_t)W * kMaxN * sizeof(T) + 15) & ~(size_t)15;
   T* lrest = reinterpret_cast<T*>(smem_raw + off);
@@ -481,17 +544,29 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   const int wvalid = (int)min((long long)W, nl - l0);
   const long long rhs = contiguous ? o : o / P.outer_per_rhs;
 
-  // ---- load
-  if (contiguous) {
-    const size_t base = (size_t)(o * P.outer_per_rhs + l0) * M;
-    for (int w = 0; w < W; ++w)
-      for (int p = threadIdx.x; p < M; p += blockDim.x)
-        tl.at(p, w) = (w < wvalid) ? ldcvt<T>(P.in, base + (size_t)w * M + p, P.in_f64) : (T)0;
-  } else {
-    const size_t base = (size_t)o * M * P.inner + l0;
-    for (int it = threadIdx.x; it < M * W; it += blockDim.x) {
-      const int p = it / W, w = it - p * W;
-      tl.at(p, w) = (w < wvalid) ? ldcvt<T>(P.in, base + (size_t)p * P.inner + w, P.in_f64) : (T)0;
+  // ---- load: tile element e = (line w, position p) is e = w M + p (contiguous lines) or
+  // e = p W + w (strided columns); 8 independent loads per thread are in flight at once.
+  const long long gbase = contiguous ? (o * P.outer_per_rhs + l0) * (long long)M : o * (long long)M * P.inner + l0;
+  const int total = M * W;
+  const int logW = 31 - __clz(W);
+  auto gaddr = [&](int e) -> long long {
+    if (contiguous) return gbase + e;
+    const int p = e >> logW, w = e & (W - 1);
+    return gbase + (long long)p * P.inner + w;
+  };
+  auto valid = [&](int e) -> bool { return contiguous ? (e < wvalid * M) : ((e & (W - 1)) < wvalid); };
+  constexpr int UNR = 8;
+  for (int e0 = threadIdx.x; e0 < total; e0 += UNR * blockDim.x) {
+    T v[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int e = e0 + u * blockDim.x;
+      v[u] = (e < total && valid(e)) ? ldcvt<T>(P.in, (size_t)gaddr(e), P.in_f64) : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < total) tile[e + (e >> TileSwz<T>::v)] = v[u];
     }
   }
   if (P.mode == kFwdScaleInv) {
@@ -515,48 +590,41 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   if (P.mode == kFwdScaleInv) {
     const T* lam = (const T*)P.lam;
     for (int it = threadIdx.x; it < M * W; it += blockDim.x) {
-      const int w = it % W, q = it / W;
+      const int w = it & (W - 1), q = it >> logW;
       tl.at(q, w) = tl.at(q, w) / (lam[q] + lrest[w]);
     }
     __syncthreads();
   }
   if (P.mode & kInv) inverse_transform<T>(tl, fbuf, save, W, n, K, P, mix, evec, tw);
 
-  // ---- store
+  // ---- store (same element order as the load)
   double s_d = 0.0, s_u = 0.0;
-  if (contiguous) {
-    const size_t base = (size_t)(o * P.outer_per_rhs + l0) * M;
-    for (int w = 0; w < wvalid; ++w)
-      for (int p = threadIdx.x; p < M; p += blockDim.x) {
-        const size_t idx = base + (size_t)w * M + p;
-        const T v = tl.at(p, w);
-        if (P.out_f64) {
-          double* out = (double*)P.out;
-          double r = (double)v;
-          if (P.accumulate) r += out[idx];
-          out[idx] = r;
-          s_d += (double)v * (double)v;
+  for (int e0 = threadIdx.x; e0 < total; e0 += UNR * blockDim.x) {
+    if (P.out_f64) {
+      double* out = (double*)P.out;
+      double prev[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int e = e0 + u * blockDim.x;
+        prev[u] = (P.accumulate && e < total && valid(e)) ? out[gaddr(e)] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < total && valid(e)) {
+          const double v = (double)tile[e + (e >> TileSwz<T>::v)];
+          const double r = prev[u] + v;
+          out[gaddr(e)] = r;
+          s_d += v * v;
           s_u += r * r;
-        } else {
-          ((float*)P.out)[idx] = (float)v;
         }
       }
-  } else {
-    const size_t base = (size_t)o * M * P.inner + l0;
-    for (int it = threadIdx.x; it < M * W; it += blockDim.x) {
-      const int p = it / W, w = it - p * W;
-      if (w >= wvalid) continue;
-      const size_t idx = base + (size_t)p * P.inner + w;
-      const T v = tl.at(p, w);
-      if (P.out_f64) {
-        double* out = (double*)P.out;
-        double r = (double)v;
-        if (P.accumulate) r += out[idx];
-        out[idx] = r;
-        s_d += (double)v * (double)v;
-        s_u += r * r;
-      } else {
-        ((float*)P.out)[idx] = (float)v;
+    } else {
+      float* out = (float*)P.out;
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < total && valid(e)) out[gaddr(e)] = (float)tile[e + (e >> TileSwz<T>::v)];
       }
     }
   }
@@ -584,23 +652,29 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   }
 }
 
+int sweep_tile_elems(int M, int W, int tsize) {
+  const long long e = (long long)M * W;
+  return (int)(e + (e >> (tsize == 4 ? TileSwz<float>::v : TileSwz<double>::v)) + 1);
+}
+
 size_t sweep_smem_bytes(int M, int n, int K, int W, int J, int tsize, bool strided) {
   (void)n;
   (void)strided;
-  size_t off = ((size_t)M * W * tsize + 15) & ~(size_t)15;
-  off += (size_t)J * 2 * K * 2 * tsize;
+  size_t off = ((size_t)sweep_tile_elems(M, W, tsize) * tsize + 15) & ~(size_t)15;
+  const int fs = tsize == 4 ? fft_stride<float>(K) : fft_stride<double>(K);
+  off += (size_t)J * 2 * fs * 2 * tsize;
   off += ((size_t)W * kMaxN * tsize + 15) & ~(size_t)15;
   off += ((size_t)W * tsize + 15) & ~(size_t)15;
   off += 2 * 32 * sizeof(double);
   return off;
 }
 
-// Largest jobs per batch with every pass's butterflies fitting the register budget.
+// Jobs per batch are limited only by shared memory (each thread loops over butterflies).
 int sweep_max_jobs(int K, int tsize, int threads) {
-  const int creg = tsize == 4 ? CReg<float>::v : CReg<double>::v;
-  const long long cap = (long long)threads * creg;   // >= nfft * K complex values
-  long long J = cap / (2LL * K);
-  return (int)(J < 1 ? 0 : J);
+  (void)K;
+  (void)tsize;
+  (void)threads;
+  return 1 << 20;
 }
 
 cudaError_t sweep_set_smem_limits() {

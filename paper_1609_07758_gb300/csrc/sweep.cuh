@@ -4,6 +4,11 @@
 #pragma once
 #include "common.cuh"
 
+// Threads per CTA of the FP32 sweep (a build-time tuning knob; FP64 sweeps use 512).
+#ifndef HOFEM_F32_THREADS
+#define HOFEM_F32_THREADS 512
+#endif
+
 namespace hofem {
 
 enum SweepMode : int { kFwd = 1, kInv = 2, kFwdScaleInv = 3 };
@@ -25,7 +30,8 @@ struct SweepParams {
   int accumulate;             // out (FP64) += result
   double* norms;              // if non-null: per rhs {sum result^2, sum out_new^2} (atomics)
   // axis tables, in the work precision T
-  const void* mix;            // (K-1) n n
+  const void* mix;            // (K-1) n NP, rows padded to NP entries
+  int mixNP;
   const void* evec;           // (n-1)^2
   const void* tw;             // 2K complex exp(-i pi t / K)
   const void* lam;            // M
@@ -37,6 +43,7 @@ struct SweepParams {
   // FFT plan for length K
   int npass;
   int radix[8];
+  int radix_log[8];
   int jobs_per_batch;
   // shared-memory layout (in elements of T)
   int ps, ws;                 // tile(p, w) = tile[p * ps + w * ws]
@@ -51,6 +58,7 @@ cudaError_t launch_sweep_f64(const SweepParams& p, cudaStream_t s);
 
 // Shared-memory bytes a sweep needs for (M, n, K, W, J) in precision of size tsize.
 size_t sweep_smem_bytes(int M, int n, int K, int W, int J, int tsize, bool strided);
+int sweep_tile_elems(int M, int W, int tsize);
 int sweep_max_jobs(int K, int tsize, int threads);
 cudaError_t sweep_set_smem_limits();
 
