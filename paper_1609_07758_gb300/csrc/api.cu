@@ -44,6 +44,7 @@ struct DevAxis {
   double *lam64 = nullptr, *mix64 = nullptr, *evec64 = nullptr, *tw64 = nullptr;
   float *lam32 = nullptr, *mix32 = nullptr, *evec32 = nullptr, *tw32 = nullptr;
   double *Aloc = nullptr, *Cloc = nullptr;
+  float* AlocLo = nullptr;
   int npass = 0, radix[8] = {0};
   int mixNP = 0;
 };
@@ -150,7 +151,7 @@ hofem_status upload(const std::vector<double>& src, T** dst, size_t* bytes) {
 void free_axis(DevAxis& a) {
   cudaFree(a.lam64); cudaFree(a.mix64); cudaFree(a.evec64); cudaFree(a.tw64);
   cudaFree(a.lam32); cudaFree(a.mix32); cudaFree(a.evec32); cudaFree(a.tw32);
-  cudaFree(a.Aloc); cudaFree(a.Cloc);
+  cudaFree(a.Aloc); cudaFree(a.Cloc); cudaFree(a.AlocLo);
   a = DevAxis{};
 }
 
@@ -345,6 +346,7 @@ hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double
   P.needPC = (out1 != nullptr) || (cCP != 0.0);
   P.needPA = cA != 0.0;
   P.Aloc = A.Aloc;
+  P.AlocLo = A.AlocLo;
   P.Cloc = A.Cloc;
   P.threads = kThreads;
   P.smem_bytes = apply_smem_bytes(A.h.n, W, E, Q_ != nullptr);
@@ -462,6 +464,7 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
     if ((st = upload(a.h.tw, &a.tw32, &tb)) != HOFEM_OK) break;
     if ((st = upload(a.h.Aloc, &a.Aloc, &tb)) != HOFEM_OK) break;
     if ((st = upload(a.h.Cloc, &a.Cloc, &tb)) != HOFEM_OK) break;
+    if ((st = upload(a.h.AlocLo, &a.AlocLo, &tb)) != HOFEM_OK) break;
     radix_plan(K[i], &a.npass, a.radix);
   }
   if (st != HOFEM_OK) {

@@ -21,7 +21,8 @@ struct AxisTables {
   std::vector<double> mix;    // (K-1) n n: [k-1][l][s], s = interior 0..n-2, n-1 = nodal
   std::vector<double> evec;   // (n-1)^2: [l][i]
   std::vector<double> tw;     // 2K complex: exp(-i pi t / K)
-  std::vector<double> Aloc;   // (n+1)^2 local stiffness, FP64
+  std::vector<double> Aloc;   // (n+1)^2 local stiffness, FP64 (high part)
+  std::vector<double> AlocLo; // (n+1)^2 remainder A - Aloc (double-double low part)
   std::vector<double> Cloc;   // (n+1)^2 local mass, FP64
 };
 

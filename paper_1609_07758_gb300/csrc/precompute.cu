@@ -404,9 +404,12 @@ hofem_status build_axis_tables(int n, int K, double X, AxisTables* out, std::str
   }
   // element matrices rounded to FP64, used by the matrix-free operator
   out->Aloc.resize(m1 * m1);
+  out->AlocLo.resize(m1 * m1);
   out->Cloc.resize(m1 * m1);
   for (int i = 0; i < m1 * m1; ++i) {
-    out->Aloc[i] = dd_to_double(A[i]);
+    const dd a = fast_two_sum(A[i].hi, A[i].lo);
+    out->Aloc[i] = a.hi;
+    out->AlocLo[i] = a.lo;
     out->Cloc[i] = dd_to_double(C[i]);
   }
 cleanup:

@@ -9,8 +9,13 @@
 // element j plus, for its node, row 0 of element j+1.
 // The stiffness is applied to differences, (A w)_a = sum_b A_ab (w_b - w_0): exactly
 // zero on constants whatever the rounding of A, which keeps the smallest eigenvalues of
-// the operator (O((k/K)^2) against O(n^2) entries) correct to FP64 accuracy -- rounding
-// the plain form would shift them by up to ~1e-9 relative for n = 9, K = 1024.
+// the operator (O((k/K)^2) against O(n^2) entries) correct -- rounding the plain form
+// would shift them by up to ~1e-9 relative for n = 9, K = 1024.  Rounding A to FP64 still
+// perturbs the element energy of smooth (locally linear) functions by ~eps |A| relative,
+// a systematic error that iterative refinement converges to (~3e-12 for n = 9, K = 1024).
+// So A is carried as a double-double hi + lo: sum_b hi_ab d_b in FP64 plus the tiny
+// correction sum_b lo_ab d_b in FP32 (it is ~1e-16 of the main term, so ~7 digits are
+// plenty), which leaves only the non-systematic FP64 accumulation rounding.
 #include "common.cuh"
 #include "residual.cuh"
 
@@ -25,9 +30,11 @@ __global__ void __launch_bounds__(512, 1) apply_kernel(const ApplyParams P) {
   double* tQ = tP + (size_t)R * W;
   double* sA = tQ + (P.Q ? (size_t)R * W : 0);
   double* sC = sA + n1 * n1;
+  float* sAlo = reinterpret_cast<float*>(sC + n1 * n1);
   for (int i = threadIdx.x; i < n1 * n1; i += blockDim.x) {
     sA[i] = P.Aloc[i];
     sC[i] = P.Cloc[i];
+    sAlo[i] = P.AlocLo[i];
   }
   const bool contiguous = (P.inner == 1);
   const long long b = blockIdx.x;
@@ -82,9 +89,15 @@ __global__ void __launch_bounds__(512, 1) apply_kernel(const ApplyParams P) {
         for (int t = 0; t <= n; ++t) pc = fma(cr[t], tP[tidx(e * n + t, w)], pc);
       }
       if (P.needPA) {
+        const float* alr = sAlo + i * n1;
+        float lo = 0.f;
 #pragma unroll
         for (int t = 1; t <= kMaxN; ++t)
-          if (t <= n) pa = fma(ar[t], dj[t], pa);
+          if (t <= n) {
+            pa = fma(ar[t], dj[t], pa);
+            lo = fmaf(alr[t], (float)dj[t], lo);
+          }
+        pa += (double)lo;
       }
       if (P.Q) {
         for (int t = 0; t <= n; ++t) qc = fma(cr[t], tQ[tidx(e * n + t, w)], qc);
@@ -94,9 +107,14 @@ __global__ void __launch_bounds__(512, 1) apply_kernel(const ApplyParams P) {
           for (int t = 0; t <= n; ++t) pc = fma(sC[t], tP[tidx((e + 1) * n + t, w)], pc);
         }
         if (P.needPA) {
+          float lo = 0.f;
 #pragma unroll
           for (int t = 1; t <= kMaxN; ++t)
-            if (t <= n) pa = fma(sA[t], dj1[t], pa);
+            if (t <= n) {
+              pa = fma(sA[t], dj1[t], pa);
+              lo = fmaf(sAlo[t], (float)dj1[t], lo);
+            }
+          pa += (double)lo;
         }
         if (P.Q) {
           for (int t = 0; t <= n; ++t) qc = fma(sC[t], tQ[tidx((e + 1) * n + t, w)], qc);
@@ -114,7 +132,7 @@ __global__ void __launch_bounds__(512, 1) apply_kernel(const ApplyParams P) {
 
 size_t apply_smem_bytes(int n, int W, int E, bool twoInputs) {
   const int R = (E + 1) * n + 1;
-  return ((size_t)R * W * (twoInputs ? 2 : 1) + 2 * (size_t)(n + 1) * (n + 1)) * sizeof(double);
+  return ((size_t)R * W * (twoInputs ? 2 : 1) + 3 * (size_t)(n + 1) * (n + 1)) * sizeof(double);
 }
 
 cudaError_t apply_set_smem_limits() {

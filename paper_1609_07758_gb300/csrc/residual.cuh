@@ -15,7 +15,8 @@ struct ApplyParams {
   const double* f;                         // if set: out2 = f - out2
   double cA, cCP, cCQ;
   int needPC, needPA;                      // which products of P are used
-  const double* Aloc;                      // (n+1)^2, device
+  const double* Aloc;                      // (n+1)^2, device (FP64 part of the stiffness)
+  const float* AlocLo;                     // (n+1)^2 remainder of the double-double stiffness
   const double* Cloc;
   int threads;
   size_t smem_bytes;
