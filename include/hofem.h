@@ -107,6 +107,20 @@ hofem_status hofem_solve(hofem_plan_t plan, const double* f, double* u, int nrhs
  * differences so that constants stay in its kernel exactly).  u, r: device FP64. */
 hofem_status hofem_apply(hofem_plan_t plan, const double* u, double* r, int nrhs, void* stream);
 
+/* r = A u exactly as hofem_apply, but allocating nothing: for callers that must not
+ * allocate device memory when they call (a framework allocator that forbids raw
+ * cudaMalloc, or a real-time loop that cannot take cudaMalloc's device-wide
+ * synchronisation).  The paper has no counterpart to this entry point.
+ * The operator's intermediate arrays (2 for N = 2, 4 for N = 3, each nrhs x unknowns
+ * doubles) live in one fixed 32 MiB device array inside the library, resident on every
+ * GPU that loads it until the process exits; nrhs x unknowns above 2,097,152 (N = 2) or
+ * 1,048,576 (N = 3) returns HOFEM_ERR_INVALID_ARG.  The first call on each device looks
+ * up that array's device address (cudaGetSymbolAddress) with the device current: make
+ * that first call before any stream capture.  All calls share the array, so calls whose
+ * work overlaps on the GPU race on it; nothing in it needs clearing between calls.
+ * u, r: device FP64, distinct.  The plan must have been created on the current device. */
+hofem_status hofem_apply_static(hofem_plan_t plan, const double* u, double* r, int nrhs, void* stream);
+
 /* r = f - A u, the FP64 residual used by iterative refinement.  f, u, r: device FP64. */
 hofem_status hofem_residual(hofem_plan_t plan, const double* f, const double* u, double* r,
                             int nrhs, void* stream);

@@ -13,6 +13,7 @@ from .binding import (  # noqa: F401
     HofemError,
     Plan,
     hofem_apply,
+    hofem_apply_static,
     hofem_destroy,
     hofem_get_eigen,
     hofem_get_info,

@@ -18,6 +18,7 @@ EXPORTED = (
     "hofem_plan", "hofem_set_refinement", "hofem_reserve", "hofem_solve", "hofem_apply",
     "hofem_residual", "hofem_transform1d", "hofem_get_eigen", "hofem_get_info",
     "hofem_destroy", "hofem_status_string", "hofem_last_error", "hofem_profile", "hofem_get_profile",
+    "hofem_apply_static",
 )
 
 
@@ -65,6 +66,7 @@ def load_library():
     lib.hofem_solve.argtypes = [P, V, V, I, V]
     lib.hofem_apply.argtypes = [P, V, V, I, V]
     lib.hofem_residual.argtypes = [P, V, V, V, I, V]
+    lib.hofem_apply_static.argtypes = [P, V, V, I, V]
     lib.hofem_transform1d.argtypes = [P, I, I, V, V, L, V]
     lib.hofem_get_eigen.argtypes = [P, I, V, V, V]
     lib.hofem_get_info.argtypes = [P, ctypes.POINTER(hofem_info)]
@@ -78,7 +80,7 @@ def load_library():
     lib.hofem_last_error.restype = ctypes.c_char_p
     for name in ("hofem_plan", "hofem_set_refinement", "hofem_reserve", "hofem_solve", "hofem_apply",
                  "hofem_residual", "hofem_transform1d", "hofem_get_eigen", "hofem_get_info",
-                 "hofem_profile", "hofem_get_profile"):
+                 "hofem_profile", "hofem_get_profile", "hofem_apply_static"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -149,6 +151,12 @@ def hofem_solve(plan, f, u, nrhs, stream=None):
 
 def hofem_apply(plan, u, r, nrhs, stream=None):
     _check(load_library().hofem_apply(plan, _ptr(u), _ptr(r), int(nrhs), _stream(stream)), "hofem_apply")
+
+
+def hofem_apply_static(plan, u, r, nrhs, stream=None):
+    """r = A u with the library's fixed device scratch (allocates nothing)."""
+    _check(load_library().hofem_apply_static(plan, _ptr(u), _ptr(r), int(nrhs), _stream(stream)),
+           "hofem_apply_static")
 
 
 def hofem_residual(plan, f, u, r, nrhs, stream=None):

@@ -378,6 +378,42 @@ hofem_status operator_apply(hofem_plan_s* p, const double* u, const double* f, d
 
 }  // namespace
 
+namespace hofem {
+size_t static_scratch_doubles();
+cudaError_t static_scratch_pointer(double** out);
+}  // namespace hofem
+
+namespace {
+
+// r = A u with the intermediates in the library's fixed device array (no allocation).
+hofem_status operator_apply_static(hofem_plan_s* p, const double* u, double* out, int nrhs, cudaStream_t s) {
+  const int N = p->N;
+  const int ntmp = N == 2 ? 2 : 4;
+  const size_t cnt = (size_t)nrhs * p->total;
+  if (cnt * ntmp > static_scratch_doubles()) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "hofem_apply_static: nrhs x unknowns = %zu exceeds the static scratch limit of %zu",
+             cnt, static_scratch_doubles() / ntmp);
+    return fail(HOFEM_ERR_INVALID_ARG, msg);
+  }
+  double* base = nullptr;
+  cudaError_t e = static_scratch_pointer(&base);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+  double* t[4] = {base, base + cnt, base + 2 * cnt, base + 3 * cnt};
+  double sc[3];
+  for (int i = 0; i < N; ++i) sc[i] = 4.0 * (double)p->K[i] * (double)p->K[i] / (p->X[i] * p->X[i]);
+  hofem_status st;
+  if (N == 2) {
+    if ((st = run_apply(p, 1, u, nullptr, t[0], t[1], nullptr, sc[1], p->alpha, 0.0, nrhs, s)) != HOFEM_OK) return st;
+    return run_apply(p, 0, t[0], t[1], nullptr, out, nullptr, sc[0], 0.0, 1.0, nrhs, s);
+  }
+  if ((st = run_apply(p, 2, u, nullptr, t[0], t[1], nullptr, sc[2], p->alpha, 0.0, nrhs, s)) != HOFEM_OK) return st;
+  if ((st = run_apply(p, 1, t[0], t[1], t[2], t[3], nullptr, sc[1], 0.0, 1.0, nrhs, s)) != HOFEM_OK) return st;
+  return run_apply(p, 0, t[2], t[3], nullptr, out, nullptr, sc[0], 0.0, 1.0, nrhs, s);
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* hofem_status_string(int s) {
@@ -560,6 +596,13 @@ hofem_status hofem_apply(hofem_plan_t p, const double* u, double* r, int nrhs, v
   if (!u || !r || nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or nrhs");
   if ((const void*)u == (const void*)r) return fail(HOFEM_ERR_INVALID_ARG, "u and r must differ");
   return operator_apply(p, u, nullptr, r, nrhs, (cudaStream_t)stream);
+}
+
+hofem_status hofem_apply_static(hofem_plan_t p, const double* u, double* r, int nrhs, void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (!u || !r || nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or nrhs");
+  if ((const void*)u == (const void*)r) return fail(HOFEM_ERR_INVALID_ARG, "u and r must differ");
+  return operator_apply_static(p, u, r, nrhs, (cudaStream_t)stream);
 }
 
 hofem_status hofem_residual(hofem_plan_t p, const double* f, const double* u, double* r, int nrhs, void* stream) {
