@@ -29,8 +29,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_ORDER, K_ELEM, X_LEN = 9, 1024, 1.0
-M_AXIS = N_ORDER * K_ELEM - 1
-UNKNOWNS = M_AXIS * M_AXIS
 METRIC = "unknowns solved/s on 1 GB300 (2D n=9 K=1024; mixed vs FP64 at 1e-12 rel err)"
 UNIT = "unknowns/s"
 PAPER_UNKNOWNS_PER_S = 84916225 / 120.0   # paper: < 2 min on a laptop (context only)
@@ -38,6 +36,7 @@ WORKLOAD = "2D unit square, n=9 Lagrange elements, K=1024 per axis, 9215^2 = 84,
 
 
 def parse_args():
+    global K_ELEM, M_AXIS, UNKNOWNS, WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
@@ -45,7 +44,16 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--refine-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--elements", type=int, default=K_ELEM,
+                    help="elements per axis (default 1024, the benchmark workload; smaller K for profiling)")
+    args = ap.parse_args()
+    K_ELEM = args.elements
+    M_AXIS = N_ORDER * K_ELEM - 1
+    UNKNOWNS = M_AXIS * M_AXIS
+    WORKLOAD = (f"2D unit square, n={N_ORDER} Lagrange elements, K={K_ELEM} per axis, "
+                f"{M_AXIS}^2 = {UNKNOWNS:,} unknowns, 1 RHS")
+    return args
 
 
 def dist_env():
@@ -188,6 +196,32 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def e2e_time(plan, f_host, f, stream, args, world, torch):
+    """ms per step through the C ABI from pinned host buffers: H2D f, solve, D2H u."""
+    fh = torch.from_numpy(f_host).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    fd = torch.empty_like(f)
+    ud = torch.empty_like(f)
+
+    def e2e_step():
+        fd.copy_(fh, non_blocking=True)
+        plan.solve(fd, ud, 1, stream)
+        uh.copy_(ud, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    e0.record(stream)
+    for _ in range(steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return max_over_ranks(e0.elapsed_time(e1) / steps, world)
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
@@ -254,29 +288,10 @@ def main():
     dominant = max(kinds, key=lambda k: kinds[k]["total_ms"])
 
     # end to end through the C ABI with host buffers: H2D of f, solve, D2H of u, every step
-    fh = torch.from_numpy(f_host).pin_memory()
-    uh = torch.empty_like(fh).pin_memory()
-    fd = torch.empty_like(f)
-    ud = torch.empty_like(f)
-
-    def e2e_step():
-        fd.copy_(fh, non_blocking=True)
-        plan.solve(fd, ud, 1, stream)
-        uh.copy_(ud, non_blocking=True)
-
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_steps = max(3, args.steps // 3)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(world)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world)
-
+    if args.no_e2e:
+        ms_e2e = float("nan")
+    else:
+        ms_e2e = e2e_time(plan, f_host, f, stream, args, world, torch)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -323,8 +338,8 @@ def main():
         "roofline": roof,
         "kernels": kinds,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * UNKNOWNS / (ms_e2e / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": 8 * UNKNOWNS, "d2h_bytes_per_step": 8 * UNKNOWNS},
+        "e2e": None if args.no_e2e else {"value": world * UNKNOWNS / (ms_e2e / 1e3), "unit": UNIT,
+                                         "h2d_bytes_per_step": 8 * UNKNOWNS, "d2h_bytes_per_step": 8 * UNKNOWNS},
         "gpu_launches": launches,
         "clocks": clock_info,
     }

@@ -3,6 +3,7 @@
 // the eigenvalue sums, inverse F_n-transforms; refined dtypes wrap low-precision solves
 // in iterative refinement with the FP64 matrix-free residual.
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -198,6 +199,16 @@ int num_jobs_host(int W, int n) { return W * ((n - 1) / 2) + (((n & 1) == 0) ? W
 // each mixing-table row), keeping >= 2 CTAs per SM when there are enough lines.
 bool choose_sweep(int M, int n, int K, int tsize, long long lines, bool strided, int* W_out, int* J_out) {
   (void)strided;
+  // tuning override "W:J" (both must fit; used to explore launch shapes)
+  if (const char* env = getenv("HOFEM_SWEEP_CFG")) {
+    int W = 0, J = 0;
+    if (sscanf(env, "%d:%d", &W, &J) == 2 && W >= 1 && (W & (W - 1)) == 0 && J >= 1 &&
+        J <= num_jobs_host(W, n) && sweep_smem_bytes(M, n, K, W, J, tsize, strided) <= kSmemLimit) {
+      *W_out = W;
+      *J_out = J;
+      return true;
+    }
+  }
   double best = 1e30;
   int bestW = 0, bestJ = 0;
   for (int W = 64; W >= 1; W >>= 1) {
@@ -217,6 +228,41 @@ bool choose_sweep(int M, int n, int K, int tsize, long long lines, bool strided,
   if (bestW == 0) return false;
   *W_out = bestW;
   *J_out = bestJ;
+  return true;
+}
+
+// Warp-FFT path (FP32, 32 <= K <= 1024): lines per CTA and warps per CTA.  Score = task
+// rounds per line (2 tasks per DST job, 32/L tasks per warp at a time), ties to larger W.
+bool choose_sweep_wfft(int M, int n, int K, long long lines, int* W_out, int* nw_out) {
+  if (const char* env = getenv("HOFEM_SWEEP_WCFG")) {
+    int W = 0, nw = 0;
+    if (sscanf(env, "%d:%d", &W, &nw) == 2 && W >= 1 && (W & (W - 1)) == 0 && (nw == 4 || nw == 8 || nw == 16) &&
+        sweep_smem_bytes_fbuf(M, W, wfft_fbuf_complex(W, n, K, nw), 4) <= kSmemLimit) {
+      *W_out = W;
+      *nw_out = nw;
+      return true;
+    }
+  }
+  const int L = K >> 5;
+  double best = 1e30;
+  int bW = 0, bN = 0;
+  for (int W = 64; W >= 1; W >>= 1) {
+    if (W > 1 && lines / W < 2 * kSMs) continue;
+    for (int nw : {16, 8}) {
+      if (sweep_smem_bytes_fbuf(M, W, wfft_fbuf_complex(W, n, K, nw), 4) > kSmemLimit) continue;
+      const int tasks = 2 * num_jobs_host(W, n);
+      const int per_round = nw * (32 / L);
+      const double score = (double)((tasks + per_round - 1) / per_round) / W;
+      if (score < best - 1e-12) {
+        best = score;
+        bW = W;
+        bN = nw;
+      }
+    }
+  }
+  if (!bW) return false;
+  *W_out = bW;
+  *nw_out = bN;
   return true;
 }
 
@@ -241,8 +287,13 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   const int tsize = f64 ? 8 : 4;
   const bool strided = g.inner > 1;
   const long long lines = nrhs * g.outer_per_rhs * g.inner;
-  int W = 1, J = 1;
-  if (!choose_sweep(A.h.M, A.h.n, A.h.K, tsize, lines, strided, &W, &J))
+  int W = 1, J = 1, nwarps = 0;
+  // the warp-register FFT path is opt-in (HOFEM_WFFT=1): on GB300 it measured slower than
+  // the block-wide DIF path (2.5 vs 2.0 ms per sweep at n = 9, K = 1024)
+  const char* wf_env = getenv("HOFEM_WFFT");
+  const bool wfft = !f64 && A.h.K >= 32 && A.h.K <= 1024 && wf_env && wf_env[0] == '1' &&
+                    choose_sweep_wfft(A.h.M, A.h.n, A.h.K, lines, &W, &nwarps);
+  if (!wfft && !choose_sweep(A.h.M, A.h.n, A.h.K, tsize, lines, strided, &W, &J))
     return fail(HOFEM_ERR_UNSUPPORTED, "no launch configuration fits shared memory for this axis");
   P.outer = nrhs * g.outer_per_rhs;
   P.inner = g.inner;
@@ -285,10 +336,13 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
     P.radix_log[i] = A.radix[i] > 0 ? 31 - __builtin_clz(A.radix[i]) : 0;
   }
   P.jobs_per_batch = J;
+  P.wfft = wfft ? 1 : 0;
+  P.wf_xs = wfft ? wfft_row_stride(A.h.K) : 0;
+  P.fbuf_complex = wfft ? wfft_fbuf_complex(W, A.h.n, A.h.K, nwarps) : sweep_fbuf_complex(A.h.K, J, tsize);
   if (strided) { P.ps = W; P.ws = 1; } else { P.ps = 1; P.ws = A.h.M; }
   P.tile_elems = sweep_tile_elems(A.h.M, W, tsize);
-  P.threads = f64 ? 512 : HOFEM_F32_THREADS;
-  P.smem_bytes = sweep_smem_bytes(A.h.M, A.h.n, A.h.K, W, J, tsize, strided);
+  P.threads = wfft ? 32 * nwarps : (f64 ? 512 : HOFEM_F32_THREADS);
+  P.smem_bytes = sweep_smem_bytes_fbuf(A.h.M, W, P.fbuf_complex, tsize);
   p->info.lines_per_cta[axis] = W;
   if (P.ntiles <= 0) return HOFEM_OK;
   const int kind = (f64 ? 0 : 3) + (mode == kFwd ? 0 : mode == kFwdScaleInv ? 1 : 2);

@@ -73,12 +73,17 @@ __global__ void __launch_bounds__(512, 1) apply_kernel(const ApplyParams P) {
     if (j > K || w >= wvalid) continue;
     // differences w_t - w_0 of P for element j and element j+1 (stiffness operand)
     double dj[kMaxN + 1], dj1[kMaxN + 1];
+    float fj[kMaxN + 1], fj1[kMaxN + 1];   // the same differences in FP32 for the lo term
     const double wp0 = tP[tidx(e * n, w)], xp0 = tP[tidx((e + 1) * n, w)];
 #pragma unroll
     for (int t = 0; t <= kMaxN; ++t)
       if (t <= n) {
         dj[t] = tP[tidx(e * n + t, w)] - wp0;
         dj1[t] = tP[tidx((e + 1) * n + t, w)] - xp0;
+        if (P.needPA) {
+          fj[t] = (float)dj[t];
+          fj1[t] = (float)dj1[t];
+        }
       }
     const int last = (j == K) ? n - 1 : n;     // node K is a Dirichlet node
     for (int i = 1; i <= last; ++i) {
@@ -95,7 +100,7 @@ __global__ void __launch_bounds__(512, 1) apply_kernel(const ApplyParams P) {
         for (int t = 1; t <= kMaxN; ++t)
           if (t <= n) {
             pa = fma(ar[t], dj[t], pa);
-            lo = fmaf(alr[t], (float)dj[t], lo);
+            lo = fmaf(alr[t], fj[t], lo);
           }
         pa += (double)lo;
       }
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(512, 1) apply_kernel(const ApplyParams P) {
           for (int t = 1; t <= kMaxN; ++t)
             if (t <= n) {
               pa = fma(sA[t], dj1[t], pa);
-              lo = fmaf(sAlo[t], (float)dj1[t], lo);
+              lo = fmaf(sAlo[t], fj1[t], lo);
             }
           pa += (double)lo;
         }

@@ -41,36 +41,34 @@ template <typename C> __device__ __forceinline__ C c_mul(C a, C b) {
   return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 
-// cos(2 pi k / 16)
-__host__ __device__ constexpr double cos16(int k) {
-  switch (k & 15) {
+// cos(2 pi k / 32), k = 0..8 (the rest by symmetry)
+__host__ __device__ constexpr double cos32_base(int k) {
+  switch (k) {
     case 0: return 1.0;
-    case 1: return 0.92387953251128675613;
-    case 2: return 0.70710678118654752440;
-    case 3: return 0.38268343236508977173;
-    case 4: return 0.0;
-    case 5: return -0.38268343236508977173;
-    case 6: return -0.70710678118654752440;
-    case 7: return -0.92387953251128675613;
-    case 8: return -1.0;
-    case 9: return -0.92387953251128675613;
-    case 10: return -0.70710678118654752440;
-    case 11: return -0.38268343236508977173;
-    case 12: return 0.0;
-    case 13: return 0.38268343236508977173;
-    case 14: return 0.70710678118654752440;
-    default: return 0.92387953251128675613;
+    case 1: return 0.98078528040323043058;
+    case 2: return 0.92387953251128673848;
+    case 3: return 0.83146961230254523567;
+    case 4: return 0.70710678118654757274;
+    case 5: return 0.55557023301960228867;
+    case 6: return 0.38268343236508983729;
+    case 7: return 0.19509032201612833135;
+    default: return 0.0;
   }
 }
 
-// b * exp(-2 pi i e / 16) for a compile-time-resolvable e
-template <typename T, typename C> __device__ __forceinline__ C tw16(C b, int e) {
-  e &= 15;
+__host__ __device__ constexpr double cos32(int k) {
+  k &= 31;
+  return k <= 8 ? cos32_base(k) : k <= 16 ? -cos32_base(16 - k) : k <= 24 ? -cos32_base(k - 16) : cos32_base(32 - k);
+}
+
+// b * exp(-2 pi i e / 32) for a compile-time-resolvable e
+template <typename T, typename C> __device__ __forceinline__ C tw32(C b, int e) {
+  e &= 31;
   if (e == 0) return b;
-  if (e == 4) return C{b.y, -b.x};
-  if (e == 8) return C{-b.x, -b.y};
-  if (e == 12) return C{-b.y, b.x};
-  const T c = (T)cos16(e), s = (T)cos16(e - 4);
+  if (e == 8) return C{b.y, -b.x};
+  if (e == 16) return C{-b.x, -b.y};
+  if (e == 24) return C{-b.y, b.x};
+  const T c = (T)cos32(e), s = (T)cos32(e - 8);
   return C{b.x * c + b.y * s, b.y * c - b.x * s};
 }
 
@@ -83,7 +81,7 @@ template <int R> __host__ __device__ constexpr int bitrev(int i) {
   return r;
 }
 
-// In-register forward DFT of R = 2, 4, 8, 16 points (iterative radix-2, natural order out).
+// In-register forward DFT of R = 1..32 points (iterative radix-2, natural order out).
 template <typename T, int R, typename C> __device__ __forceinline__ void dft_reg(C (&v)[R]) {
 #pragma unroll
   for (int i = 0; i < R; ++i) {
@@ -101,7 +99,7 @@ template <typename T, int R, typename C> __device__ __forceinline__ void dft_reg
 #pragma unroll
       for (int k = 0; k < half; ++k) {
         C a = v[s + k];
-        C b = tw16<T>(v[s + k + half], k * (16 / (2 * half)));
+        C b = tw32<T>(v[s + k + half], k * (32 / (2 * half)));
         v[s + k] = c_add(a, b);
         v[s + k + half] = c_sub(a, b);
       }
@@ -110,6 +108,8 @@ template <typename T, int R, typename C> __device__ __forceinline__ void dft_reg
 }
 
 template <int R> struct Log2;
+template <> struct Log2<1> { static constexpr int v = 0; };
+template <> struct Log2<32> { static constexpr int v = 5; };
 template <> struct Log2<2> { static constexpr int v = 1; };
 template <> struct Log2<4> { static constexpr int v = 2; };
 template <> struct Log2<8> { static constexpr int v = 3; };
@@ -312,12 +312,13 @@ __device__ __forceinline__ void dst_out(const typename Cx<T>::type* buf, int jb,
 // Per-frequency n x n mixing, one thread per frequency k looping over the tile's lines
 // two at a time; row l of G_k = (q_1..q_{n-1}, c) of mode (k, l) is read with 16-byte
 // vector loads from a table whose rows are padded to NP (a multiple of 4) entries.
+// Generic-address loads: `row` points into shared memory (staged tables) or global memory.
 template <typename T, int N>
-__device__ __forceinline__ void load_row(const T* __restrict__ row, T (&g)[N]) {
+__device__ __forceinline__ void load_row(const T* row, T (&g)[N]) {
   if constexpr (sizeof(T) == 4) {
 #pragma unroll
     for (int s = 0; s < N; s += 4) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(row) + s / 4);
+      const float4 v = reinterpret_cast<const float4*>(row)[s / 4];
       g[s] = v.x;
       if (s + 1 < N) g[s + 1] = v.y;
       if (s + 2 < N) g[s + 2] = v.z;
@@ -326,54 +327,90 @@ __device__ __forceinline__ void load_row(const T* __restrict__ row, T (&g)[N]) {
   } else {
 #pragma unroll
     for (int s = 0; s < N; s += 2) {
-      const double2 v = __ldg(reinterpret_cast<const double2*>(row) + s / 2);
+      const double2 v = reinterpret_cast<const double2*>(row)[s / 2];
       g[s] = v.x;
       if (s + 1 < N) g[s + 1] = v.y;
     }
   }
 }
 
+// Block stride (elements of T) of one G_k in the shared staging area: N NP rounded so
+// that consecutive blocks start an odd number of 16-byte units apart (conflict-free
+// 16-byte loads by consecutive threads).
+template <typename T, int N> __device__ __forceinline__ int stage_stride(int NP) {
+  constexpr int per16 = 16 / (int)sizeof(T);
+  const int b = N * NP;
+  return ((b / per16) & 1) ? b : b + per16;
+}
+
 template <typename T, int N, bool FWD>
-__device__ __noinline__ void mix_impl(const Tile<T> tl, int W, int K, const T* __restrict__ mix, int NP,
-                         const T* __restrict__ evec, T* save, T scale, T scale0) {
+__device__ __forceinline__ void mix_one_k(const Tile<T>& tl, int W, int k, const T* Gk, int NP, T scale) {
   constexpr int LC = 2;
-  for (int k = 1 + threadIdx.x; k < K; k += blockDim.x) {
-    const T* Gk = mix + (size_t)(k - 1) * N * NP;
-    const int base = (k - 1) * N;
-    for (int w0 = 0; w0 < W; w0 += LC) {
-      T x[LC][N], y[LC][N];
+  const int base = (k - 1) * N;
+  for (int w0 = 0; w0 < W; w0 += LC) {
+    T x[LC][N], y[LC][N];
 #pragma unroll
-      for (int c = 0; c < LC; ++c)
+    for (int c = 0; c < LC; ++c)
 #pragma unroll
-        for (int s = 0; s < N; ++s) {
-          x[c][s] = (w0 + c < W) ? tl.at(base + s, w0 + c) : (T)0;
-          y[c][s] = (T)0;
-        }
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        T g[N];
-        load_row<T, N>(Gk + l * NP, g);
-        if (FWD) {
-#pragma unroll
-          for (int c = 0; c < LC; ++c) {
-            T acc = (T)0;
-#pragma unroll
-            for (int s = 0; s < N; ++s) acc = fma(g[s], x[c][s], acc);
-            y[c][l] = acc * scale;
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < LC; ++c)
-#pragma unroll
-            for (int s = 0; s < N; ++s) y[c][s] = fma(g[s], x[c][l], y[c][s]);
-        }
+      for (int s = 0; s < N; ++s) {
+        x[c][s] = (w0 + c < W) ? tl.at(base + s, w0 + c) : (T)0;
+        y[c][s] = (T)0;
       }
 #pragma unroll
-      for (int c = 0; c < LC; ++c)
-        if (w0 + c < W)
+    for (int l = 0; l < N; ++l) {
+      T g[N];
+      load_row<T, N>(Gk + l * NP, g);
+      if (FWD) {
 #pragma unroll
-          for (int s = 0; s < N; ++s) tl.at(base + s, w0 + c) = FWD ? y[c][s] : y[c][s] * scale;
+        for (int c = 0; c < LC; ++c) {
+          T acc = (T)0;
+#pragma unroll
+          for (int s = 0; s < N; ++s) acc = fma(g[s], x[c][s], acc);
+          y[c][l] = acc * scale;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < LC; ++c)
+#pragma unroll
+          for (int s = 0; s < N; ++s) y[c][s] = fma(g[s], x[c][l], y[c][s]);
+      }
     }
+#pragma unroll
+    for (int c = 0; c < LC; ++c)
+      if (w0 + c < W)
+#pragma unroll
+        for (int s = 0; s < N; ++s) tl.at(base + s, w0 + c) = FWD ? y[c][s] : y[c][s] * scale;
+  }
+}
+
+// The mixing tables are staged through shared memory (the FFT buffers, idle during the
+// mixing) in chunks of frequencies with coalesced 16-byte copies, then read from there;
+// reading them straight from L2 thread by thread was latency-bound.
+template <typename T, int N, bool FWD>
+__device__ __noinline__ void mix_impl(const Tile<T> tl, int W, int K, const T* __restrict__ mix, int NP,
+                                      const T* __restrict__ evec, T* save, T scale, T scale0, T* stage,
+                                      int stage_cap) {
+  const int BS = stage_stride<T, N>(NP);
+  const int CK = stage_cap / BS;
+  if (CK >= 32) {
+    constexpr int per16 = 16 / (int)sizeof(T);
+    const int vec_per_block = (N * NP) / per16;
+    for (int k0 = 1; k0 < K; k0 += CK) {
+      const int nk = min(CK, K - k0);
+      const int4* src = reinterpret_cast<const int4*>(mix + (size_t)(k0 - 1) * N * NP);
+      const int nvec = nk * vec_per_block;
+      for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+        const int kb = v / vec_per_block, r = v - kb * vec_per_block;
+        reinterpret_cast<int4*>(stage + (size_t)kb * BS)[r] = __ldg(src + v);
+      }
+      __syncthreads();
+      for (int k = k0 + threadIdx.x; k < k0 + nk; k += blockDim.x)
+        mix_one_k<T, N, FWD>(tl, W, k, stage + (size_t)(k - k0) * BS, NP, scale);
+      __syncthreads();
+    }
+  } else {
+    for (int k = 1 + threadIdx.x; k < K; k += blockDim.x)
+      mix_one_k<T, N, FWD>(tl, W, k, mix + (size_t)(k - 1) * N * NP, NP, scale);
   }
   // k = 0 block: w_0 = E t / K (forward, t in the tile) or g = E^T w_0 (inverse, into save)
   if constexpr (N > 1) {
@@ -405,10 +442,10 @@ __device__ __noinline__ void mix_impl(const Tile<T> tl, int W, int K, const T* _
 
 template <typename T, bool FWD>
 __device__ __forceinline__ void mix_dispatch(const Tile<T> tl, int W, int n, int K, const T* __restrict__ mix, int NP,
-                             const T* __restrict__ evec, T* save, T scale, T scale0) {
+                             const T* __restrict__ evec, T* save, T scale, T scale0, T* stage, int stage_cap) {
   switch (n) {
 #define HOFEM_MIX_CASE(NN) \
-  case NN: mix_impl<T, NN, FWD>(tl, W, K, mix, NP, evec, save, scale, scale0); break;
+  case NN: mix_impl<T, NN, FWD>(tl, W, K, mix, NP, evec, save, scale, scale0, stage, stage_cap); break;
     HOFEM_MIX_CASE(1) HOFEM_MIX_CASE(2) HOFEM_MIX_CASE(3) HOFEM_MIX_CASE(4)
     HOFEM_MIX_CASE(5) HOFEM_MIX_CASE(6) HOFEM_MIX_CASE(7) HOFEM_MIX_CASE(8)
     HOFEM_MIX_CASE(9) HOFEM_MIX_CASE(10) HOFEM_MIX_CASE(11) HOFEM_MIX_CASE(12)
@@ -464,7 +501,8 @@ __device__ void forward_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
   }
   __syncthreads();
   // mixing: w_k = G_k xhat_k / (2K)  (the DST outputs above are 2 x DST)
-  mix_dispatch<T, true>(tl, W, n, K, mix, P.mixNP, evec, tsave, (T)(0.5 / K), (T)(1.0 / K));
+  mix_dispatch<T, true>(tl, W, n, K, mix, P.mixNP, evec, tsave, (T)(0.5 / K), (T)(1.0 / K),
+                        reinterpret_cast<T*>(fbuf), 2 * P.fbuf_complex);
   __syncthreads();
 }
 
@@ -473,7 +511,8 @@ __device__ void inverse_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
                                   int K, const SweepParams& P, const T* __restrict__ mix,
                                   const T* __restrict__ evec, const typename Cx<T>::type* __restrict__ tw) {
   // mixing: xhat_k = G_k^T w_k / 2 (the DST below returns 2 x DST); g = E^T w_0
-  mix_dispatch<T, false>(tl, W, n, K, mix, P.mixNP, evec, gsave, (T)0.5, (T)1.0);
+  mix_dispatch<T, false>(tl, W, n, K, mix, P.mixNP, evec, gsave, (T)0.5, (T)1.0,
+                         reinterpret_cast<T*>(fbuf), 2 * P.fbuf_complex);
   __syncthreads();
   const int logK = 31 - __clz(K);
   const int logW = 31 - __clz(W);
@@ -515,11 +554,222 @@ __device__ void inverse_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Warp-register FFT path (FP32, K = 32 L with L = 1..32 lanes per FFT).
+//
+// A DST job (pair a + ib) needs the K-point FFTs of u (even outputs) and v (odd
+// outputs); each is a "task" run by a group of L lanes with 32 complex values per lane:
+// lane r holds x[r + L n2], n2 = 0..31.  With n = r + L n2 and k = k2 + 32 k1,
+//   X[k2 + 32 k1] = sum_r w_L^{r k1} [ w_K^{r k2} sum_n2 x[r + L n2] w_32^{n2 k2} ]:
+// a 32-point DFT in registers, a twiddle, one transpose through padded shared memory
+// within the group, and 32/L L-point DFTs in registers.  The pre-combined sequences of
+// every job of the tile are first staged in shared memory (region X); tasks then read
+// X and write their outputs straight to the tile, with warp-level synchronisation only.
+
+template <int L> struct WGeom {
+  // complex elements of one lane group's transpose area (rows of L + 1, groups offset by
+  // an odd multiple of L complex so the groups of a warp use different banks)
+  static constexpr int rows = 32 * (L + 1);
+  static constexpr int group = ((rows + 31) / 32) * 32 + L;
+  static constexpr int warp = L == 1 ? 0 : (32 / L) * group;
+};
+
+__host__ __device__ inline int wfft_warp_scratch(int L) {
+  switch (L) {
+    case 1: return WGeom<1>::warp;
+    case 2: return WGeom<2>::warp;
+    case 4: return WGeom<4>::warp;
+    case 8: return WGeom<8>::warp;
+    case 16: return WGeom<16>::warp;
+    default: return WGeom<32>::warp;
+  }
+}
+
+// In place on v: on return v[t L + k1] = X[(r + L t) + 32 k1].
+template <int L>
+__device__ __forceinline__ void wfft_core(float2 (&v)[32], float2* sg, int r, const float2* __restrict__ tw, int K) {
+  dft_reg<float, 32>(v);
+  if (L == 1) return;
+  if (r != 0) {
+    const int m2 = 2 * K - 1;
+#pragma unroll
+    for (int k2 = 1; k2 < 32; ++k2) v[k2] = c_mul(v[k2], __ldg(tw + ((2 * r * k2) & m2)));
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < 32; ++k2) sg[k2 * (L + 1) + r] = v[k2];
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < 32 / L; ++t) {
+    const int k2 = r + L * t;
+    float2 u[L];
+#pragma unroll
+    for (int n1 = 0; n1 < L; ++n1) u[n1] = sg[k2 * (L + 1) + n1];
+    dft_reg<float, L>(u);
+#pragma unroll
+    for (int k1 = 0; k1 < L; ++k1) v[t * L + k1] = u[k1];
+  }
+  __syncwarp();
+}
+
+// Stage x_j = (a_j, b_j), j = 0..K-1 (x_0 = 0) of every job into X (row stride XS).
+__device__ void wfft_build_x(const Tile<float> tl, float2* X, int XS, int njobs, int W, int n, int K, bool inverse) {
+  const int logK = 31 - __clz(K), logW = 31 - __clz(W);
+  const int items = njobs << logK;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int jb = it >> logK, j = it & (K - 1);
+    const Job job = job_of(jb, W, logW, n);
+    X[jb * XS + j] = pair_x(tl, job, j, n, K, inverse);
+  }
+}
+
+// Run every (job, half) task; outputs 2 x DST of a (-Im) and of b (Re) at index k.
+template <int L>
+__device__ __noinline__ void wfft_tasks(const Tile<float> tl, const float2* X, int XS, float2* scratch, int njobs,
+                                        int W, int n, int K, const float2* __restrict__ tw) {
+  constexpr int G = 32 / L;                     // tasks per warp at a time
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int grp = lane / L, r = lane - grp * L;
+  float2* sg = scratch + (size_t)warp * WGeom<L>::warp + grp * WGeom<L>::group;
+  const int ntasks = 2 * njobs, half = K >> 1, logW = 31 - __clz(W);
+  for (int base = warp * G; base < ntasks; base += nwarps * G) {
+    const int task = base + grp;
+    const bool active = task < ntasks;
+    const int jb = active ? (task >> 1) : 0, h = task & 1;
+    const float2* x = X + jb * XS;
+    float2 v[32];
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) {
+      const int i = r + L * n2;
+      float2 val = make_float2(0.f, 0.f);
+      if (active && i != 0) {
+        const float2 xa = x[i], xb = x[K - i];
+        val = h == 0 ? c_sub(xa, xb) : c_mul(c_add(xa, xb), __ldg(tw + i));
+      }
+      v[n2] = val;
+    }
+    wfft_core<L>(v, sg, r, tw, K);
+    if (!active) continue;
+    const Job job = job_of(jb, W, logW, n);
+    const int sa = slot_of(job.ma, n), sb = job.mb >= 0 ? slot_of(job.mb, n) : 0;
+#pragma unroll
+    for (int t = 0; t < G; ++t)
+#pragma unroll
+      for (int k1 = 0; k1 < L; ++k1) {
+        const int m = r + L * t + 32 * k1;
+        if (m >= half) continue;
+        const int k = 2 * m + h;               // U gives even k, V odd k
+        if (k == 0) continue;
+        const float2 o = v[t * L + k1];
+        tl.at((k - 1) * n + sa, job.wa) = -o.y;
+        if (job.mb >= 0) tl.at((k - 1) * n + sb, job.wb) = o.x;
+      }
+  }
+}
+
+// Inverse post-combine of one job (by one warp): D at rows of its components -> physical
+// v_{j-1/2} = D_{j-1} + P D_j + (-P)^{j-1} g (nodes are already in place).  Lanes own
+// contiguous j ranges and walk them downwards; each first reads the value below its range.
+__device__ void wfft_postcombine(const Tile<float> tl, const float* gsave, int njobs, int W, int n, int K) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int logW = 31 - __clz(W);
+  const int per = (K + 31) / 32;                // j values per lane
+  for (int jb = warp; jb < njobs; jb += nwarps) {
+    const Job job = job_of(jb, W, logW, n);
+    if (job.ma == 0 && job.mb <= 0) continue;   // nodes only
+    const int m = n - 1;
+    int ci, cc, w;                              // components (ci, cc) of line w; cc = ci for the middle one
+    if (job.ma == 0) { ci = job.mb; cc = job.mb; w = job.wb; }
+    else { ci = job.ma; cc = job.mb; w = job.wa; }
+    const float gi = gsave[w * m + ci - 1], gc = gsave[w * m + cc - 1];
+    auto Di = [&](int j) -> float { return (j >= 1 && j <= K - 1) ? tl.at((j - 1) * n + ci - 1, w) : 0.f; };
+    auto Dc = [&](int j) -> float { return (j >= 1 && j <= K - 1) ? tl.at((j - 1) * n + cc - 1, w) : 0.f; };
+    const int jlo = 1 + lane * per, jhi = min(K, jlo + per - 1);
+    float below_i = 0.f, below_c = 0.f;
+    if (jlo <= K) { below_i = Di(jlo - 1); below_c = Dc(jlo - 1); }
+    __syncwarp();
+    for (int j = jhi; j >= jlo; --j) {
+      const float di_prev = (j == jlo) ? below_i : Di(j - 1);
+      const float dc_prev = (j == jlo) ? below_c : Dc(j - 1);
+      const float di = Di(j), dc = Dc(j);
+      const bool odd = j & 1;
+      const float vi = di_prev + dc + (odd ? gi : -gc);
+      const float vc = dc_prev + di + (odd ? gc : -gi);
+      tl.at((j - 1) * n + ci - 1, w) = vi;
+      if (cc != ci) tl.at((j - 1) * n + cc - 1, w) = vc;
+    }
+    __syncwarp();
+  }
+}
+
+template <int L>
+__device__ void wfft_forward(const Tile<float>& tl, float2* X, int XS, float2* scratch, float* tsave, int W, int n,
+                             int K, const SweepParams& P, const float* __restrict__ mix,
+                             const float* __restrict__ evec, const float2* __restrict__ tw, int stage_cap) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int logW = 31 - __clz(W);
+  for (int item = warp; item < W * (n - 1); item += nwarps) {
+    const int w = item & (W - 1), i = (item >> logW) + 1;
+    float acc = 0.f;
+    for (int j = 1 + lane; j <= K; j += 32) {
+      const float v = tl.at((j - 1) * n + ((j & 1) ? i : n - i) - 1, w);
+      acc += (j & 1) ? v : -v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) tsave[w * (n - 1) + i - 1] = acc;
+  }
+  const int njobs = num_jobs(W, n);
+  wfft_build_x(tl, X, XS, njobs, W, n, K, false);
+  __syncthreads();
+  wfft_tasks<L>(tl, X, XS, scratch, njobs, W, n, K, tw);
+  __syncthreads();
+  for (int it = threadIdx.x; it < W * (n - 1); it += blockDim.x) {
+    const int w = it & (W - 1), i = it >> logW;
+    tl.at((K - 1) * n + i, w) = tsave[w * (n - 1) + i];
+  }
+  __syncthreads();
+  mix_dispatch<float, true>(tl, W, n, K, mix, P.mixNP, evec, tsave, 0.5f / K, 1.0f / K, reinterpret_cast<float*>(X),
+                            stage_cap);
+  __syncthreads();
+}
+
+template <int L>
+__device__ void wfft_inverse(const Tile<float>& tl, float2* X, int XS, float2* scratch, float* gsave, int W, int n,
+                             int K, const SweepParams& P, const float* __restrict__ mix,
+                             const float* __restrict__ evec, const float2* __restrict__ tw, int stage_cap) {
+  mix_dispatch<float, false>(tl, W, n, K, mix, P.mixNP, evec, gsave, 0.5f, 1.0f, reinterpret_cast<float*>(X),
+                             stage_cap);
+  __syncthreads();
+  const int njobs = num_jobs(W, n);
+  wfft_build_x(tl, X, XS, njobs, W, n, K, true);
+  __syncthreads();
+  wfft_tasks<L>(tl, X, XS, scratch, njobs, W, n, K, tw);
+  __syncthreads();
+  wfft_postcombine(tl, gsave, njobs, W, n, K);
+  __syncthreads();
+}
+
+template <bool FWD>
+__device__ void wfft_dispatch(const Tile<float>& tl, float2* X, int XS, float2* scratch, float* save, int W, int n,
+                              int K, const SweepParams& P, const float* mix, const float* evec, const float2* tw,
+                              int stage_cap) {
+  switch (K >> 5) {
+#define HOFEM_WF_CASE(LL)                                                                                   \
+  case LL:                                                                                                 \
+    if (FWD) wfft_forward<LL>(tl, X, XS, scratch, save, W, n, K, P, mix, evec, tw, stage_cap);            \
+    else wfft_inverse<LL>(tl, X, XS, scratch, save, W, n, K, P, mix, evec, tw, stage_cap);                \
+    break;
+    HOFEM_WF_CASE(1) HOFEM_WF_CASE(2) HOFEM_WF_CASE(4) HOFEM_WF_CASE(8) HOFEM_WF_CASE(16) HOFEM_WF_CASE(32)
+#undef HOFEM_WF_CASE
+    default: break;
+  }
+}
+
 template <typename T> __device__ __forceinline__ T ldcvt(const void* p, size_t i, int f64) {
   return f64 ? (T)__ldg((const double*)p + i) : (T)__ldg((const float*)p + i);
 }
 
-template <typename T>
+template <typename T, bool WF>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) sweep_kernel(const SweepParams P) {
   using C = typename Cx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -528,7 +778,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
   T* tile = reinterpret_cast<T*>(smem_raw);
   size_t off = ((size_t)P.tile_elems * sizeof(T) + 15) & ~(size_t)15;
   C* fbuf = reinterpret_cast<C*>(smem_raw + off);
-  off += (size_t)P.jobs_per_batch * 2 * fft_stride<T>(K) * sizeof(C);
+  off += (size_t)P.fbuf_complex * sizeof(C);
   T* save = reinterpret_cast<T*>(smem_raw + off);
   off += ((size_t)W * kMaxN * sizeof(T) + 15) & ~(size_t)15;
   T* lrest = reinterpret_cast<T*>(smem_raw + off);
@@ -555,7 +805,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
     return gbase + (long long)p * P.inner + w;
   };
   auto valid = [&](int e) -> bool { return contiguous ? (e < wvalid * M) : ((e & (W - 1)) < wvalid); };
-  constexpr int UNR = 8;
+  constexpr int UNR = HOFEM_LOAD_UNROLL;
   for (int e0 = threadIdx.x; e0 < total; e0 += UNR * blockDim.x) {
     T v[UNR];
 #pragma unroll
@@ -586,7 +836,13 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
   const T* mix = (const T*)P.mix;
   const T* evec = (const T*)P.evec;
   const C* tw = (const C*)P.tw;
-  if (P.mode & kFwd) forward_transform<T>(tl, fbuf, save, W, n, K, P, mix, evec, tw);
+  if constexpr (WF && sizeof(T) == 4) {
+    if (P.mode & kFwd)
+      wfft_dispatch<true>(tl, fbuf, P.wf_xs, fbuf + (size_t)num_jobs(W, n) * P.wf_xs, save, W, n, K, P, mix, evec,
+                          tw, 2 * P.fbuf_complex);
+  } else {
+    if (P.mode & kFwd) forward_transform<T>(tl, fbuf, save, W, n, K, P, mix, evec, tw);
+  }
   if (P.mode == kFwdScaleInv) {
     const T* lam = (const T*)P.lam;
     for (int it = threadIdx.x; it < M * W; it += blockDim.x) {
@@ -595,7 +851,13 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
     }
     __syncthreads();
   }
-  if (P.mode & kInv) inverse_transform<T>(tl, fbuf, save, W, n, K, P, mix, evec, tw);
+  if constexpr (WF && sizeof(T) == 4) {
+    if (P.mode & kInv)
+      wfft_dispatch<false>(tl, fbuf, P.wf_xs, fbuf + (size_t)num_jobs(W, n) * P.wf_xs, save, W, n, K, P, mix, evec,
+                           tw, 2 * P.fbuf_complex);
+  } else {
+    if (P.mode & kInv) inverse_transform<T>(tl, fbuf, save, W, n, K, P, mix, evec, tw);
+  }
 
   // ---- store (same element order as the load)
   double s_d = 0.0, s_u = 0.0;
@@ -657,6 +919,27 @@ int sweep_tile_elems(int M, int W, int tsize) {
   return (int)(e + (e >> (tsize == 4 ? TileSwz<float>::v : TileSwz<double>::v)) + 1);
 }
 
+long long sweep_fbuf_complex(int K, int J, int tsize) {
+  const int fs = tsize == 4 ? fft_stride<float>(K) : fft_stride<double>(K);
+  return (long long)J * 2 * fs;
+}
+
+// Warp-FFT path (FP32, 32 <= K <= 1024): X rows of K + L complex for every job of the
+// tile, then one transpose area per warp.
+int wfft_row_stride(int K) { return K + (K >> 5); }
+long long wfft_fbuf_complex(int W, int n, int K, int nwarps) {
+  return (long long)num_jobs(W, n) * wfft_row_stride(K) + (long long)nwarps * wfft_warp_scratch(K >> 5);
+}
+
+size_t sweep_smem_bytes_fbuf(int M, int W, long long fbuf_complex, int tsize) {
+  size_t off = ((size_t)sweep_tile_elems(M, W, tsize) * tsize + 15) & ~(size_t)15;
+  off += (size_t)fbuf_complex * 2 * tsize;
+  off += ((size_t)W * kMaxN * tsize + 15) & ~(size_t)15;
+  off += ((size_t)W * tsize + 15) & ~(size_t)15;
+  off += 2 * 32 * sizeof(double);
+  return off;
+}
+
 size_t sweep_smem_bytes(int M, int n, int K, int W, int J, int tsize, bool strided) {
   (void)n;
   (void)strided;
@@ -678,18 +961,21 @@ int sweep_max_jobs(int K, int tsize, int threads) {
 }
 
 cudaError_t sweep_set_smem_limits() {
-  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(sweep_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  e = cudaFuncSetAttribute(sweep_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sweep_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
 }
 
 cudaError_t launch_sweep_f32(const SweepParams& p, cudaStream_t s) {
-  sweep_kernel<float><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
+  if (p.wfft) sweep_kernel<float, true><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
+  else sweep_kernel<float, false><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sweep_f64(const SweepParams& p, cudaStream_t s) {
-  sweep_kernel<double><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
+  sweep_kernel<double, false><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
   return cudaGetLastError();
 }
 

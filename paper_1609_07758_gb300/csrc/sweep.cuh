@@ -9,6 +9,12 @@
 #define HOFEM_F32_THREADS 512
 #endif
 
+// Independent global loads in flight per thread in the load/store phases of a sweep
+// (bytes in flight per SM bound the achievable HBM bandwidth of these phases).
+#ifndef HOFEM_LOAD_UNROLL
+#define HOFEM_LOAD_UNROLL 8
+#endif
+
 namespace hofem {
 
 enum SweepMode : int { kFwd = 1, kInv = 2, kFwdScaleInv = 3 };
@@ -45,6 +51,9 @@ struct SweepParams {
   int radix[8];
   int radix_log[8];
   int jobs_per_batch;
+  long long fbuf_complex;     // complex elements of the FFT region (batched buffers or X + transposes)
+  int wfft;                   // 1: warp-register FFT path (FP32, 32 <= K <= 1024)
+  int wf_xs;                  // row stride (complex) of the staged sequences X
   // shared-memory layout (in elements of T)
   int ps, ws;                 // tile(p, w) = tile[p * ps + w * ws]
   int tile_elems;
@@ -59,6 +68,10 @@ cudaError_t launch_sweep_f64(const SweepParams& p, cudaStream_t s);
 // Shared-memory bytes a sweep needs for (M, n, K, W, J) in precision of size tsize.
 size_t sweep_smem_bytes(int M, int n, int K, int W, int J, int tsize, bool strided);
 int sweep_tile_elems(int M, int W, int tsize);
+long long sweep_fbuf_complex(int K, int J, int tsize);
+int wfft_row_stride(int K);
+long long wfft_fbuf_complex(int W, int n, int K, int nwarps);
+size_t sweep_smem_bytes_fbuf(int M, int W, long long fbuf_complex, int tsize);
 int sweep_max_jobs(int K, int tsize, int threads);
 cudaError_t sweep_set_smem_limits();
 

@@ -162,3 +162,23 @@ def test_refinement_reports_its_progress():
     torch.cuda.synchronize()
     info = plan.info()
     assert info.converged == 1 and 1 <= info.iterations <= 8 and info.last_rel_update <= 1e-13
+
+
+@pytest.mark.parametrize("n,K,lines", [(2, 32, 5), (9, 64, 3), (4, 512, 6), (3, 1024, 2)])
+def test_warp_fft_path_matches_oracle(monkeypatch, n, K, lines):
+    """The opt-in warp-register FFT path (FP32, 32 <= K <= 1024) gives the same transforms."""
+    monkeypatch.setenv("HOFEM_WFFT", "1")
+    plan = H().Plan(2, [K, K], n, [1.0, 1.0], 1)
+    s = spectrum.spectrum(n, K, 1.0)
+    S = s.dense_S()
+    M = n * K - 1
+    rng = np.random.default_rng(5)
+    y = rng.standard_normal((lines, M))
+    out = torch.zeros(lines, M, dtype=torch.float64, device="cuda")
+    fac = np.sqrt(s.norm / K)
+    plan.transform1d(0, 0, dev(y), out, lines)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), s.forward(y, S) * fac) <= 3e-6
+    plan.transform1d(0, 1, dev(y), out, lines)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), s.inverse(y / fac, S)) <= 3e-6
