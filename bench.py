@@ -298,9 +298,10 @@ def main():
     except OSError:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    n1 = N_ORDER + 1
-    # algorithmic work per launch (per unknown x unknowns): see DESIGN.md, "Rooflines"
-    fp64_flops_apply = 2 * 2 * n1 * n1 / N_ORDER * UNKNOWNS       # two sum-factorised 1D products
+    h_odd, h_even = (N_ORDER + 1) // 2, N_ORDER // 2 + 1
+    # algorithmic work per launch (per unknown x unknowns): one operator sweep applies two
+    # folded element matrices, 2 (h_even^2 + h_odd^2) flops each per element and line
+    fp64_flops_apply = 2 * 2 * (h_even ** 2 + h_odd ** 2) / N_ORDER * UNKNOWNS
     sweep_bytes = {"sweep_fwd_f32": 12.0, "sweep_fsi_f32": 8.0, "sweep_inv_f32": 20.0,
                    "sweep_fwd_f64": 16.0, "sweep_fsi_f64": 16.0, "sweep_inv_f64": 16.0}
     d = kinds[dominant]

@@ -2,6 +2,7 @@
 // Algorithm (a) of Sect. 2 par. 4: direct F_n-transforms along every axis, division by
 // the eigenvalue sums, inverse F_n-transforms; refined dtypes wrap low-precision solves
 // in iterative refinement with the FP64 matrix-free residual.
+#include <algorithm>
 #include <chrono>
 #include <cstdlib>
 #include <cmath>
@@ -44,8 +45,6 @@ struct DevAxis {
   AxisTables h;
   double *lam64 = nullptr, *mix64 = nullptr, *evec64 = nullptr, *tw64 = nullptr;
   float *lam32 = nullptr, *mix32 = nullptr, *evec32 = nullptr, *tw32 = nullptr;
-  double *Aloc = nullptr, *Cloc = nullptr;
-  float* AlocLo = nullptr;
   int npass = 0, radix[8] = {0};
   int mixNP = 0;
 };
@@ -152,7 +151,6 @@ hofem_status upload(const std::vector<double>& src, T** dst, size_t* bytes) {
 void free_axis(DevAxis& a) {
   cudaFree(a.lam64); cudaFree(a.mix64); cudaFree(a.evec64); cudaFree(a.tw64);
   cudaFree(a.lam32); cudaFree(a.mix32); cudaFree(a.evec32); cudaFree(a.tw32);
-  cudaFree(a.Aloc); cudaFree(a.Cloc); cudaFree(a.AlocLo);
   a = DevAxis{};
 }
 
@@ -368,16 +366,26 @@ hofem_status solve_once(hofem_plan_s* p, const double* f, double* u, int nrhs, b
   return run_sweep(p, N - 1, kInv, f64, work, f64, u, true, accumulate, norms, nrhs, s);
 }
 
+// One operator sweep along `axis` (modes in residual.cuh): Q == nullptr is the first
+// sweep (out1 required), Q and out1 a middle one, Q without out1 the last one.
 hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double* Q_, double* out1, double* out2,
-                       const double* f, double cA, double cCP, double cCQ, int nrhs, cudaStream_t s) {
+                       const double* f, double cA, double cCP, int nrhs, cudaStream_t s) {
   const DevAxis& A = p->ax[axis];
   Geo g = geometry(p, axis);
   const bool strided = g.inner > 1;
   ApplyParams P{};
-  int W = strided ? 32 : 4;
-  int E = strided ? 16 : 64;
-  while (apply_smem_bytes(A.h.n, W, E, Q_ != nullptr) > kSmemLimit && E > 1) E /= 2;
+  const int W = kApplyLines;
+  int E = 8;
+  if (const char* env = getenv("HOFEM_APPLY_E")) {
+    const int e = atoi(env);
+    if (e >= 1 && e <= 256) E = e;
+  }
+  while (apply_smem_bytes(A.h.n, E) > kSmemLimit && E > 1) E /= 2;
   E = std::min(E, A.h.K);
+  P.mode = Q_ == nullptr ? kApplyFirst : (out1 != nullptr ? kApplyMid : kApplyLast);
+  if ((P.mode != kApplyLast) != (out1 != nullptr) || (P.mode == kApplyLast && cCP != 0.0) ||
+      (P.mode != kApplyLast && f != nullptr))
+    return fail(HOFEM_ERR_INVALID_ARG, "operator sweep: inconsistent arguments");
   P.outer = (long long)nrhs * g.outer_per_rhs;
   P.inner = g.inner;
   P.outer_per_rhs = g.outer_per_rhs;
@@ -394,16 +402,15 @@ hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double
   P.out1 = out1;
   P.out2 = out2;
   P.f = f;
-  P.cA = cA;
+  P.cA = cA * A.h.a_scale;
   P.cCP = cCP;
-  P.cCQ = cCQ;
-  P.needPC = (out1 != nullptr) || (cCP != 0.0);
-  P.needPA = cA != 0.0;
-  P.Aloc = A.Aloc;
-  P.AlocLo = A.AlocLo;
-  P.Cloc = A.Cloc;
-  P.threads = kThreads;
-  P.smem_bytes = apply_smem_bytes(A.h.n, W, E, Q_ != nullptr);
+  std::copy(A.h.CfE.begin(), A.h.CfE.end(), P.CE);
+  std::copy(A.h.CfO.begin(), A.h.CfO.end(), P.CO);
+  std::copy(A.h.AfE.begin(), A.h.AfE.end(), P.AE);
+  std::copy(A.h.AfO.begin(), A.h.AfO.end(), P.AO);
+  for (size_t i = 0; i < A.h.AfELo.size(); ++i) P.AEl[i] = (float)A.h.AfELo[i];
+  for (size_t i = 0; i < A.h.AfOLo.size(); ++i) P.AOl[i] = (float)A.h.AfOLo[i];
+  P.smem_bytes = apply_smem_bytes(A.h.n, E);
   if (P.ntiles <= 0) return HOFEM_OK;
   cudaError_t e = timed_launch(p, 6, s, [&]() { return launch_apply(P, s); });
   if (e != cudaSuccess) return cuda_fail(e, "operator launch");
@@ -421,13 +428,13 @@ hofem_status operator_apply(hofem_plan_s* p, const double* u, const double* f, d
   double** t = p->tmp64;
   if (N == 2) {
     // axis 1: T1 = u xC, T2 = s1 (u xA) + alpha (u xC); axis 0: out = [f -] (s0 T1 xA + T2 xC)
-    if ((st = run_apply(p, 1, u, nullptr, t[0], t[1], nullptr, sc[1], p->alpha, 0.0, nrhs, s)) != HOFEM_OK) return st;
-    return run_apply(p, 0, t[0], t[1], nullptr, out, f, sc[0], 0.0, 1.0, nrhs, s);
+    if ((st = run_apply(p, 1, u, nullptr, t[0], t[1], nullptr, sc[1], p->alpha, nrhs, s)) != HOFEM_OK) return st;
+    return run_apply(p, 0, t[0], t[1], nullptr, out, f, sc[0], 0.0, nrhs, s);
   }
   // N == 3
-  if ((st = run_apply(p, 2, u, nullptr, t[0], t[1], nullptr, sc[2], p->alpha, 0.0, nrhs, s)) != HOFEM_OK) return st;
-  if ((st = run_apply(p, 1, t[0], t[1], t[2], t[3], nullptr, sc[1], 0.0, 1.0, nrhs, s)) != HOFEM_OK) return st;
-  return run_apply(p, 0, t[2], t[3], nullptr, out, f, sc[0], 0.0, 1.0, nrhs, s);
+  if ((st = run_apply(p, 2, u, nullptr, t[0], t[1], nullptr, sc[2], p->alpha, nrhs, s)) != HOFEM_OK) return st;
+  if ((st = run_apply(p, 1, t[0], t[1], t[2], t[3], nullptr, sc[1], 0.0, nrhs, s)) != HOFEM_OK) return st;
+  return run_apply(p, 0, t[2], t[3], nullptr, out, f, sc[0], 0.0, nrhs, s);
 }
 
 }  // namespace
@@ -458,12 +465,12 @@ hofem_status operator_apply_static(hofem_plan_s* p, const double* u, double* out
   for (int i = 0; i < N; ++i) sc[i] = 4.0 * (double)p->K[i] * (double)p->K[i] / (p->X[i] * p->X[i]);
   hofem_status st;
   if (N == 2) {
-    if ((st = run_apply(p, 1, u, nullptr, t[0], t[1], nullptr, sc[1], p->alpha, 0.0, nrhs, s)) != HOFEM_OK) return st;
-    return run_apply(p, 0, t[0], t[1], nullptr, out, nullptr, sc[0], 0.0, 1.0, nrhs, s);
+    if ((st = run_apply(p, 1, u, nullptr, t[0], t[1], nullptr, sc[1], p->alpha, nrhs, s)) != HOFEM_OK) return st;
+    return run_apply(p, 0, t[0], t[1], nullptr, out, nullptr, sc[0], 0.0, nrhs, s);
   }
-  if ((st = run_apply(p, 2, u, nullptr, t[0], t[1], nullptr, sc[2], p->alpha, 0.0, nrhs, s)) != HOFEM_OK) return st;
-  if ((st = run_apply(p, 1, t[0], t[1], t[2], t[3], nullptr, sc[1], 0.0, 1.0, nrhs, s)) != HOFEM_OK) return st;
-  return run_apply(p, 0, t[2], t[3], nullptr, out, nullptr, sc[0], 0.0, 1.0, nrhs, s);
+  if ((st = run_apply(p, 2, u, nullptr, t[0], t[1], nullptr, sc[2], p->alpha, nrhs, s)) != HOFEM_OK) return st;
+  if ((st = run_apply(p, 1, t[0], t[1], t[2], t[3], nullptr, sc[1], 0.0, nrhs, s)) != HOFEM_OK) return st;
+  return run_apply(p, 0, t[2], t[3], nullptr, out, nullptr, sc[0], 0.0, nrhs, s);
 }
 
 }  // namespace
@@ -552,9 +559,6 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
     if ((st = upload(a.h.lam, &a.lam32, &tb)) != HOFEM_OK) break;
     if ((st = upload(a.h.evec, &a.evec32, &tb)) != HOFEM_OK) break;
     if ((st = upload(a.h.tw, &a.tw32, &tb)) != HOFEM_OK) break;
-    if ((st = upload(a.h.Aloc, &a.Aloc, &tb)) != HOFEM_OK) break;
-    if ((st = upload(a.h.Cloc, &a.Cloc, &tb)) != HOFEM_OK) break;
-    if ((st = upload(a.h.AlocLo, &a.AlocLo, &tb)) != HOFEM_OK) break;
     radix_plan(K[i], &a.npass, a.radix);
   }
   if (st != HOFEM_OK) {

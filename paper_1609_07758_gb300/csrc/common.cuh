@@ -12,6 +12,9 @@ namespace hofem {
 constexpr int kMaxN = 16;       // largest element order
 constexpr int kMaxK = 8192;     // largest elements per axis (power of two)
 constexpr int kMaxDims = 3;
+// Orders whose element stiffness, scaled by the common denominator of its entries, is an
+// integer matrix exactly representable in FP64; larger orders carry it as hi + lo.
+constexpr int kExactStiffnessMaxN = 9;
 
 // Host copy of one axis' eigen-data and twiddles (FP64), built at plan time.
 struct AxisTables {
@@ -21,9 +24,17 @@ struct AxisTables {
   std::vector<double> mix;    // (K-1) n n: [k-1][l][s], s = interior 0..n-2, n-1 = nodal
   std::vector<double> evec;   // (n-1)^2: [l][i]
   std::vector<double> tw;     // 2K complex: exp(-i pi t / K)
-  std::vector<double> Aloc;   // (n+1)^2 local stiffness, FP64 (high part)
-  std::vector<double> AlocLo; // (n+1)^2 remainder A - Aloc (double-double low part)
-  std::vector<double> Cloc;   // (n+1)^2 local mass, FP64
+  // Even/odd folded local matrices (centro-symmetry R M R = M): for h = (n+1)/2 pairs
+  // (t, n-t) and, for even n, the middle point, rows r < hr = n/2 + 1:
+  //   E[r][t] = (M[r][t] + M[r][n-t]) / 2 (t < h),  E[r][mid] = M[r][mid],
+  //   O[r][t] = (M[r][t] - M[r][n-t]) / 2 (r, t < h),
+  // so (M w)_r = E_r + O_r and (M w)_{n-r} = E_r - O_r with the folded w.
+  std::vector<double> CfE, CfO;          // mass, FP64   (hr x hr, h x h)
+  // Stiffness: for n <= 9 the integer matrix D A (exact; lo parts zero, a_scale = 1/D),
+  // else A as double-double hi + lo (a_scale = 1).
+  std::vector<double> AfE, AfO;
+  std::vector<double> AfELo, AfOLo;
+  double a_scale = 1.0;
 };
 
 hofem_status build_axis_tables(int n, int K, double X, AxisTables* out, std::string* err);

@@ -159,6 +159,63 @@ void element_matrices_dd(int n, std::vector<dd>& A, std::vector<dd>& C) {
     }
 }
 
+// Integer form of the element stiffness.  On [-1, 1], A_ab = (n/2) int_0^n N_a' N_b' dx /
+// (d_a d_b) with the node polynomials N_a(x) = prod_{c != a} (x - c) (integer coefficients,
+// nodes 0..n) and d_a = prod_{c != a} (a - c), |d_a| = a! (n-a)! a divisor of n!; the
+// integral of x^k over [0, n] is n^{k+1}/(k+1) with k <= 2n-2.  So D0 = 2 (n!)^2
+// lcm(1..2n-1) clears every denominator, and D = D0 / gcd(D0, all D0 A_ab) is the least
+// common one.  D0 A_ab is rounded from the double-double entries (their error is far
+// below 1/2 for n <= 9).  Returns false unless every D A_ab is below 2^52 in magnitude
+// and every row of D A sums to zero exactly (A annihilates constants).
+static bool stiffness_integers(int n, const std::vector<dd>& A, std::vector<double>* S, double* inv_D) {
+  if (n < 1 || n > kExactStiffnessMaxN) return false;
+  typedef __int128 i128;
+  auto gcd = [](i128 a, i128 b) {
+    if (a < 0) a = -a;
+    if (b < 0) b = -b;
+    while (b != 0) {
+      const i128 t = a % b;
+      a = b;
+      b = t;
+    }
+    return a;
+  };
+  i128 fact = 1, L = 1;
+  for (int i = 2; i <= n; ++i) fact *= i;
+  for (int i = 2; i <= 2 * n - 1; ++i) L = L / gcd(L, i) * i;
+  const i128 D0 = 2 * fact * fact * L;
+  const double d_hi = (double)D0;
+  const dd Dd = fast_two_sum(d_hi, (double)(D0 - (i128)d_hi));
+  const int m1 = n + 1;
+  std::vector<i128> Z(m1 * m1);
+  i128 g = D0;
+  for (int i = 0; i < m1 * m1; ++i) {
+    const dd z = A[i] * Dd;
+    const double a = nearbyint(z.hi);
+    const double rem = (z.hi - a) + z.lo;
+    const double b = nearbyint(rem);
+    if (fabs(rem - b) > 1e-6) return false;
+    Z[i] = (i128)a + (i128)b;
+    g = gcd(g, Z[i]);
+  }
+  const i128 D = D0 / g;
+  const i128 lim = (i128)1 << 52;
+  if (D >= lim) return false;
+  S->assign(m1 * m1, 0.0);
+  for (int r = 0; r < m1; ++r) {
+    i128 row = 0;
+    for (int c = 0; c < m1; ++c) {
+      const i128 v = Z[r * m1 + c] / g;
+      if (v >= lim || -v >= lim) return false;
+      row += v;
+      (*S)[r * m1 + c] = (double)v;
+    }
+    if (row != 0) return false;
+  }
+  *inv_D = 1.0 / (double)D;
+  return true;
+}
+
 // ----------------------------------------------------------------- device: eigen
 struct EigInput {
   int n, K;
@@ -402,15 +459,58 @@ hofem_status build_axis_tables(int n, int K, double X, AxisTables* out, std::str
     out->tw[2 * t] = dd_to_double(c);
     out->tw[2 * t + 1] = -dd_to_double(s);
   }
-  // element matrices rounded to FP64, used by the matrix-free operator
-  out->Aloc.resize(m1 * m1);
-  out->AlocLo.resize(m1 * m1);
-  out->Cloc.resize(m1 * m1);
-  for (int i = 0; i < m1 * m1; ++i) {
-    const dd a = fast_two_sum(A[i].hi, A[i].lo);
-    out->Aloc[i] = a.hi;
-    out->AlocLo[i] = a.lo;
-    out->Cloc[i] = dd_to_double(C[i]);
+  // folded element matrices for the matrix-free operator
+  {
+    const int h = (n + 1) / 2, hr = n / 2 + 1;
+    const bool mid = (n % 2) == 0;
+    std::vector<double> S;
+    double inv_D = 1.0;
+    const bool exact = stiffness_integers(n, A, &S, &inv_D);
+    if (n <= kExactStiffnessMaxN && !exact) {
+      if (err) *err = "element stiffness is not an exact FP64 integer matrix after scaling";
+      st = HOFEM_ERR_UNSUPPORTED;
+      goto cleanup;
+    }
+    out->a_scale = exact ? inv_D : 1.0;
+    out->CfE.assign(hr * hr, 0.0);
+    out->AfE.assign(hr * hr, 0.0);
+    out->AfELo.assign(hr * hr, 0.0);
+    out->CfO.assign(h * h, 0.0);
+    out->AfO.assign(h * h, 0.0);
+    out->AfOLo.assign(h * h, 0.0);
+    // stiffness entry (r, t) of the folded tables as hi + lo (lo = 0 when exact)
+    auto fold = [&](int r, int t, double sign, double w, double* hi, double* lo) {
+      if (exact) {
+        *hi = (S[r * m1 + t] + sign * S[r * m1 + (n - t)]) * w;   // integers < 2^52: exact
+        *lo = 0.0;
+      } else {
+        const dd a = (A[r * m1 + t] + A[r * m1 + (n - t)] * sign) * w;
+        const dd v = fast_two_sum(a.hi, a.lo);
+        *hi = v.hi;
+        *lo = v.lo;
+      }
+    };
+    for (int r = 0; r < hr; ++r) {
+      for (int t = 0; t < h; ++t) {
+        out->CfE[r * hr + t] = dd_to_double((C[r * m1 + t] + C[r * m1 + (n - t)]) * 0.5);
+        fold(r, t, 1.0, 0.5, &out->AfE[r * hr + t], &out->AfELo[r * hr + t]);
+        if (r < h) {
+          out->CfO[r * h + t] = dd_to_double((C[r * m1 + t] - C[r * m1 + (n - t)]) * 0.5);
+          fold(r, t, -1.0, 0.5, &out->AfO[r * h + t], &out->AfOLo[r * h + t]);
+        }
+      }
+      if (mid) {
+        const int t = n / 2;
+        out->CfE[r * hr + t] = dd_to_double(C[r * m1 + t]);
+        if (exact) {
+          out->AfE[r * hr + t] = S[r * m1 + t];
+        } else {
+          const dd v = fast_two_sum(A[r * m1 + t].hi, A[r * m1 + t].lo);
+          out->AfE[r * hr + t] = v.hi;
+          out->AfELo[r * hr + t] = v.lo;
+        }
+      }
+    }
   }
 cleanup:
   cudaFree(d_base);

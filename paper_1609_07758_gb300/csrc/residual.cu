@@ -1,41 +1,156 @@
 // Matrix-free FP64 operator of Eq. bvp glob 2,
 //     A u = sum_i 4 h_i^-2 A_i (x) prod_{m!=i} C_m u + alpha C_1 (x) ... (x) C_N u,
-// evaluated as one banded 1D sweep per axis (sum factorisation over the tensor product).
-// A sweep along axis a reads up to two arrays P, Q and writes
-//     out1 = P x_a C,    out2 = cA (P x_a A) + cCP (P x_a C) + cCQ (Q x_a C)
-// (optionally out2 := f - out2).  The 1D products are element by element: element j's
-// local vector w (n+1 values, Dirichlet nodes = 0) is multiplied by the local C and by
-// the local A; unknown p owned by element j (local points 1..n) collects rows 1..n of
-// element j plus, for its node, row 0 of element j+1.
+// evaluated as one banded 1D sweep per axis (sum factorisation over the tensor product);
+// the three sweep kinds are listed with ApplyMode in residual.cuh.  The 1D products are
+// element by element: element j's local vector w (n+1 values, Dirichlet nodes = 0) is
+// multiplied by the local C and by the local A; unknown p owned by element j (local
+// points 1..n) collects rows 1..n of element j plus, for its node, row 0 of element j+1.
+//
 // The stiffness is applied to differences, (A w)_a = sum_b A_ab (w_b - w_0): exactly
-// zero on constants whatever the rounding of A, which keeps the smallest eigenvalues of
-// the operator (O((k/K)^2) against O(n^2) entries) correct -- rounding the plain form
-// would shift them by up to ~1e-9 relative for n = 9, K = 1024.  Rounding A to FP64 still
-// perturbs the element energy of smooth (locally linear) functions by ~eps |A| relative,
-// a systematic error that iterative refinement converges to (~3e-12 for n = 9, K = 1024).
-// So A is carried as a double-double hi + lo: sum_b hi_ab d_b in FP64 plus the tiny
-// correction sum_b lo_ab d_b in FP32 (it is ~1e-16 of the main term, so ~7 digits are
-// plenty), which leaves only the non-systematic FP64 accumulation rounding.
+// zero on constants whatever the rounding, which keeps the smallest eigenvalues of the
+// operator (O((k/K)^2) against O(n^2) entries) correct.  The table itself must not be
+// rounded either: a rounded A perturbs the element energy of smooth (locally linear)
+// functions by ~eps |A| relative, a systematic error that iterative refinement converges
+// to (~3e-12 for n = 9, K = 1024).  For n <= 9 the table is D A with D the common
+// denominator of A's entries -- integers below 2^52, exact in FP64 -- and 1/D is folded
+// into the sweep's scalar coefficient, which only rescales the whole term by 1 + O(eps).
+// For larger n, A is a double-double hi + lo: sum_b hi_ab d_b in FP64 plus the tiny
+// correction sum_b lo_ab d_b in FP32 (~1e-16 of the main term, so ~7 digits suffice).
+//
+// Folding: with w_e[t] = w_t + w_{n-t}, w_o[t] = w_t - w_{n-t} (t < h = (n+1)/2) and the
+// middle value for even n, rows r and n-r of M w are E_r + O_r and E_r - O_r, which
+// halves the products.  The odd part of the differences is w_o itself.
 #include "common.cuh"
 #include "residual.cuh"
 
 namespace hofem {
 
-__global__ void __launch_bounds__(512, 1) apply_kernel(const ApplyParams P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = P.n, K = P.K, M = P.M, W = P.W, E = P.E;
-  const int n1 = n + 1;
-  const int R = (E + 1) * n + 1;       // tile rows: node j0-1 .. node j0+E
-  double* tP = reinterpret_cast<double*>(smem_raw);
-  double* tQ = tP + (size_t)R * W;
-  double* sA = tQ + (P.Q ? (size_t)R * W : 0);
-  double* sC = sA + n1 * n1;
-  float* sAlo = reinterpret_cast<float*>(sC + n1 * n1);
-  for (int i = threadIdx.x; i < n1 * n1; i += blockDim.x) {
-    sA[i] = P.Aloc[i];
-    sC[i] = P.Cloc[i];
-    sAlo[i] = P.AlocLo[i];
+namespace {
+
+constexpr int kLd = kApplyLines + 1;   // tile row stride in doubles (odd: no bank conflicts)
+
+// All rows of one element (HALO: only its row 0) for line w; `base` is the tile row of
+// the element's left node, `s` its slot index.  The products run column by column
+// (outer-product order), so only the row accumulators and one folded pair are live.
+// Interior rows are written back into the tiles in place (tP <- P x C, tQ <- out2),
+// which only this element reads; rows 0 and n go to the slot arrays for the node sums.
+template <int N, int MODE, bool HALO>
+__device__ __forceinline__ void element_rows(const ApplyParams& P, double* tP, double* tQ, int base, int w,
+                                             double* sV0, double* sP0, double* sVn, double* sPn, int s) {
+  constexpr int n = N, h = (N + 1) / 2, hr = N / 2 + 1;
+  constexpr bool has_mid = (N % 2) == 0;
+  constexpr bool LO = N > kExactStiffnessMaxN;
+  constexpr bool PC = MODE != kApplyLast;    // P x C is wanted
+  constexpr bool QC = MODE != kApplyFirst;   // Q x C is wanted
+  constexpr int rE = HALO ? 1 : hr, rO = HALO ? 1 : h;   // rows computed
+  double cE[hr], cO[h], aE[hr], aO[h], qE[hr], qO[h];
+  float lE[hr], lO[h];
+  const double* cp = tP + (size_t)base * kLd + w;
+  const double* cq = tQ + (size_t)base * kLd + w;
+  const double w0 = cp[0];
+  // column t: folded values pe, po (P), de (differences; their odd part is po), qe, qo (Q)
+  auto column = [&](int t, bool middle, double pe, double po, double de, double qe, double qo) {
+#pragma unroll
+    for (int r = 0; r < rE; ++r) {
+      const double ce = P.CE[r * hr + t], ae = P.AE[r * hr + t];
+      if (t == 0) {
+        if (PC) cE[r] = ce * pe;
+        aE[r] = ae * de;
+        if (LO) lE[r] = P.AEl[r * hr + t] * (float)de;
+        if (QC) qE[r] = ce * qe;
+      } else {
+        if (PC) cE[r] = fma(ce, pe, cE[r]);
+        aE[r] = fma(ae, de, aE[r]);
+        if (LO) lE[r] = fmaf(P.AEl[r * hr + t], (float)de, lE[r]);
+        if (QC) qE[r] = fma(ce, qe, qE[r]);
+      }
+    }
+    if (middle) return;
+#pragma unroll
+    for (int r = 0; r < rO; ++r) {
+      const double co = P.CO[r * h + t], ao = P.AO[r * h + t];
+      if (t == 0) {
+        if (PC) cO[r] = co * po;
+        aO[r] = ao * po;
+        if (LO) lO[r] = P.AOl[r * h + t] * (float)po;
+        if (QC) qO[r] = co * qo;
+      } else {
+        if (PC) cO[r] = fma(co, po, cO[r]);
+        aO[r] = fma(ao, po, aO[r]);
+        if (LO) lO[r] = fmaf(P.AOl[r * h + t], (float)po, lO[r]);
+        if (QC) qO[r] = fma(co, qo, qO[r]);
+      }
+    }
+  };
+#pragma unroll
+  for (int t = 0; t < h; ++t) {
+    const double a = cp[t * kLd], c = cp[(n - t) * kLd];
+    double qa = 0.0, qc = 0.0;
+    if (QC) {
+      qa = cq[t * kLd];
+      qc = cq[(n - t) * kLd];
+    }
+    column(t, false, a + c, a - c, t == 0 ? c - w0 : (a - w0) + (c - w0), qa + qc, qa - qc);
   }
+  if (has_mid) {
+    const double a = cp[(n / 2) * kLd];
+    column(hr - 1, true, a, 0.0, a - w0, QC ? cq[(n / 2) * kLd] : 0.0, 0.0);
+  }
+  const double cA = P.cA, cCP = P.cCP;
+  const bool alpha = PC && cCP != 0.0;
+  auto put = [&](int i, double pc, double v) {
+    if (i == 0) {
+      sV0[s] = v;
+      if (PC) sP0[s] = pc;
+    } else if (i == n) {
+      sVn[s] = v;
+      if (PC) sPn[s] = pc;
+    } else {
+      tQ[(size_t)(base + i) * kLd + w] = v;
+      if (PC) tP[(size_t)(base + i) * kLd + w] = pc;
+    }
+  };
+#pragma unroll
+  for (int r = 0; r < rE; ++r) {
+    double ae = aE[r], ao = r < h ? aO[r] : 0.0;
+    if (LO) {
+      ae += (double)lE[r];
+      if (r < h) ao += (double)lO[r];
+    }
+    const double ce = PC ? cE[r] : 0.0, co = PC && r < h ? cO[r] : 0.0;
+    // even and odd parts of out2
+    double se = QC ? fma(cA, ae, qE[r]) : cA * ae;
+    double so = r < h ? (QC ? fma(cA, ao, qO[r]) : cA * ao) : 0.0;
+    if (alpha) {
+      se = fma(cCP, ce, se);
+      if (r < h) so = fma(cCP, co, so);
+    }
+    if (r < h) {
+      put(r, ce + co, se + so);
+      if (!HALO) put(n - r, ce - co, se - so);
+    } else {
+      put(r, ce, se);                    // middle row of an even order
+    }
+  }
+}
+
+// One CTA: W lines x E consecutive elements.  The tile holds dofs of tile rows 0..R-1 =
+// left node of the segment .. right node of the halo element j0+E (row 0 of which closes
+// the segment's last node).  Loads and stores are coalesced along whichever of line or
+// dof index is contiguous in memory.
+template <int N, int MODE>
+__global__ void __launch_bounds__(kApplyThreads, N <= 10 ? 2 : 1) apply_kernel(const __grid_constant__ ApplyParams P) {
+  constexpr int n = N, W = kApplyLines;
+  constexpr bool PC = MODE != kApplyLast, QC = MODE != kApplyFirst;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = P.M, E = P.E;
+  const int R = (E + 1) * n + 1;
+  double* tP = reinterpret_cast<double*>(smem_raw);
+  double* tQ = tP + (size_t)R * kLd;
+  double* sV0 = tQ + (size_t)R * kLd;   // [E+1][W]
+  double* sP0 = sV0 + (size_t)(E + 1) * W;
+  double* sVn = sP0 + (size_t)(E + 1) * W;   // [E][W]
+  double* sPn = sVn + (size_t)E * W;
   const bool contiguous = (P.inner == 1);
   const long long b = blockIdx.x;
   const long long seg = b % P.seg_per_line;
@@ -44,108 +159,112 @@ __global__ void __launch_bounds__(512, 1) apply_kernel(const ApplyParams P) {
   const long long l0 = tix * W;
   const long long nl = contiguous ? P.outer_per_rhs : P.inner;
   const int wvalid = (int)min((long long)W, nl - l0);
-  const int j0 = (int)(seg * E) + 1;   // first element of the segment (1-based)
-  const long long p0 = (long long)(j0 - 1) * n - 1;   // dof of tile row 0
-  // tile(r, w): contiguous -> [w][r], strided -> [r][w]
-  auto tidx = [&](int r, int w) -> size_t { return contiguous ? (size_t)w * R + r : (size_t)r * W + w; };
+  const long long p0 = (long long)seg * E * n - 1;   // dof of tile row 0
   auto gidx = [&](long long p, int w) -> size_t {
-    return contiguous ? (size_t)(o * P.outer_per_rhs + l0 + w) * M + p
-                      : ((size_t)o * M + p) * P.inner + l0 + w;
+    return contiguous ? (size_t)(o * P.outer_per_rhs + l0 + w) * M + p : ((size_t)o * M + p) * P.inner + l0 + w;
   };
   for (int it = threadIdx.x; it < R * W; it += blockDim.x) {
     int r, w;
-    if (contiguous) { w = it / R; r = it - w * R; } else { r = it / W; w = it - r * W; }
+    if (contiguous) {
+      w = it / R;
+      r = it - w * R;
+    } else {
+      r = it / W;
+      w = it - r * W;
+    }
     const long long p = p0 + r;
     double vp = 0.0, vq = 0.0;
     if (w < wvalid && p >= 0 && p < M) {
-      vp = __ldg(P.P + gidx(p, w));
-      if (P.Q) vq = __ldg(P.Q + gidx(p, w));
+      const size_t g = gidx(p, w);
+      vp = __ldg(P.P + g);
+      if (QC) vq = __ldg(P.Q + g);
     }
-    tP[tidx(r, w)] = vp;
-    if (P.Q) tQ[tidx(r, w)] = vq;
+    tP[(size_t)r * kLd + w] = vp;
+    if (QC) tQ[(size_t)r * kLd + w] = vq;
   }
   __syncthreads();
-  const int items = E * W;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    int e, w;
-    if (contiguous) { w = it / E; e = it - w * E; } else { e = it / W; w = it - e * W; }
-    const int j = j0 + e;
-    if (j > K || w >= wvalid) continue;
-    // differences w_t - w_0 of P for element j and element j+1 (stiffness operand)
-    double dj[kMaxN + 1], dj1[kMaxN + 1];
-    float fj[kMaxN + 1], fj1[kMaxN + 1];   // the same differences in FP32 for the lo term
-    const double wp0 = tP[tidx(e * n, w)], xp0 = tP[tidx((e + 1) * n, w)];
-#pragma unroll
-    for (int t = 0; t <= kMaxN; ++t)
-      if (t <= n) {
-        dj[t] = tP[tidx(e * n + t, w)] - wp0;
-        dj1[t] = tP[tidx((e + 1) * n + t, w)] - xp0;
-        if (P.needPA) {
-          fj[t] = (float)dj[t];
-          fj1[t] = (float)dj1[t];
-        }
-      }
-    const int last = (j == K) ? n - 1 : n;     // node K is a Dirichlet node
-    for (int i = 1; i <= last; ++i) {
-      double pc = 0.0, pa = 0.0, qc = 0.0;
-      const double* cr = sC + i * n1;
-      const double* ar = sA + i * n1;
-      if (P.needPC) {
-        for (int t = 0; t <= n; ++t) pc = fma(cr[t], tP[tidx(e * n + t, w)], pc);
-      }
-      if (P.needPA) {
-        const float* alr = sAlo + i * n1;
-        float lo = 0.f;
-#pragma unroll
-        for (int t = 1; t <= kMaxN; ++t)
-          if (t <= n) {
-            pa = fma(ar[t], dj[t], pa);
-            lo = fmaf(alr[t], fj[t], lo);
-          }
-        pa += (double)lo;
-      }
-      if (P.Q) {
-        for (int t = 0; t <= n; ++t) qc = fma(cr[t], tQ[tidx(e * n + t, w)], qc);
-      }
-      if (i == n) {                              // node j: add row 0 of element j+1
-        if (P.needPC) {
-          for (int t = 0; t <= n; ++t) pc = fma(sC[t], tP[tidx((e + 1) * n + t, w)], pc);
-        }
-        if (P.needPA) {
-          float lo = 0.f;
-#pragma unroll
-          for (int t = 1; t <= kMaxN; ++t)
-            if (t <= n) {
-              pa = fma(sA[t], dj1[t], pa);
-              lo = fmaf(sAlo[t], fj1[t], lo);
-            }
-          pa += (double)lo;
-        }
-        if (P.Q) {
-          for (int t = 0; t <= n; ++t) qc = fma(sC[t], tQ[tidx((e + 1) * n + t, w)], qc);
-        }
-      }
-      const long long p = (long long)(j - 1) * n + i - 1;
-      const size_t g = gidx(p, w);
-      if (P.out1) P.out1[g] = pc;
-      double v = P.cA * pa + P.cCP * pc + P.cCQ * qc;
-      if (P.f) v = __ldg(P.f + g) - v;
-      P.out2[g] = v;
+  for (int it = threadIdx.x; it < E * W; it += blockDim.x) {
+    const int e = it / W, w = it - e * W;
+    element_rows<N, MODE, false>(P, tP, tQ, e * n, w, sV0, sP0, sVn, sPn, it);
+  }
+  for (int w = threadIdx.x; w < W; w += blockDim.x)
+    element_rows<N, MODE, true>(P, tP, tQ, E * n, w, sV0, sP0, sVn, sPn, E * W + w);
+  __syncthreads();
+  // node rows (e+1) n: row n of element e + row 0 of element e+1
+  for (int it = threadIdx.x; it < E * W; it += blockDim.x) {
+    const int e = it / W, w = it - e * W;
+    const size_t row = (size_t)(e + 1) * n * kLd + w;
+    tQ[row] = sVn[it] + sV0[it + W];
+    if (PC) tP[row] = sPn[it] + sP0[it + W];
+  }
+  __syncthreads();
+  // tile rows 1 .. E n are this segment's dofs
+  const int Rs = E * n;
+  for (int it = threadIdx.x; it < Rs * W; it += blockDim.x) {
+    int r, w;
+    if (contiguous) {
+      w = it / Rs;
+      r = it - w * Rs + 1;
+    } else {
+      r = it / W + 1;
+      w = it - (r - 1) * W;
     }
+    const long long p = p0 + r;
+    if (w >= wvalid || p >= M) continue;
+    const size_t g = gidx(p, w);
+    double v = tQ[(size_t)r * kLd + w];
+    if (MODE == kApplyLast && P.f) v = __ldg(P.f + g) - v;
+    P.out2[g] = v;
+    if (PC) P.out1[g] = tP[(size_t)r * kLd + w];
   }
 }
 
-size_t apply_smem_bytes(int n, int W, int E, bool twoInputs) {
-  const int R = (E + 1) * n + 1;
-  return ((size_t)R * W * (twoInputs ? 2 : 1) + 3 * (size_t)(n + 1) * (n + 1)) * sizeof(double);
+}  // namespace
+
+size_t apply_smem_bytes(int n, int E) {
+  const size_t R = (size_t)(E + 1) * n + 1;
+  return (2 * R * kLd + 2 * (size_t)(E + 1) * kApplyLines + 2 * (size_t)E * kApplyLines) * sizeof(double);
+}
+
+template <int N> static cudaError_t set_limit() {
+  cudaError_t e = cudaFuncSetAttribute(apply_kernel<N, kApplyFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(apply_kernel<N, kApplyMid>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(apply_kernel<N, kApplyLast>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  return e;
 }
 
 cudaError_t apply_set_smem_limits() {
-  return cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  cudaError_t e = cudaSuccess;
+#define HOFEM_AP_LIMIT(NN) if (e == cudaSuccess) e = set_limit<NN>();
+  HOFEM_AP_LIMIT(1) HOFEM_AP_LIMIT(2) HOFEM_AP_LIMIT(3) HOFEM_AP_LIMIT(4) HOFEM_AP_LIMIT(5) HOFEM_AP_LIMIT(6)
+  HOFEM_AP_LIMIT(7) HOFEM_AP_LIMIT(8) HOFEM_AP_LIMIT(9) HOFEM_AP_LIMIT(10) HOFEM_AP_LIMIT(11) HOFEM_AP_LIMIT(12)
+  HOFEM_AP_LIMIT(13) HOFEM_AP_LIMIT(14) HOFEM_AP_LIMIT(15) HOFEM_AP_LIMIT(16)
+#undef HOFEM_AP_LIMIT
+  return e;
+}
+
+template <int N> static void launch_n(const ApplyParams& p, cudaStream_t s) {
+  const dim3 grid((unsigned)p.ntiles), block(kApplyThreads);
+  switch (p.mode) {
+    case kApplyFirst: apply_kernel<N, kApplyFirst><<<grid, block, p.smem_bytes, s>>>(p); break;
+    case kApplyMid: apply_kernel<N, kApplyMid><<<grid, block, p.smem_bytes, s>>>(p); break;
+    default: apply_kernel<N, kApplyLast><<<grid, block, p.smem_bytes, s>>>(p); break;
+  }
 }
 
 cudaError_t launch_apply(const ApplyParams& p, cudaStream_t s) {
-  apply_kernel<<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
+  if (p.mode < kApplyFirst || p.mode > kApplyLast) return cudaErrorInvalidValue;
+  switch (p.n) {
+#define HOFEM_AP_CASE(NN) \
+  case NN: launch_n<NN>(p, s); break;
+    HOFEM_AP_CASE(1) HOFEM_AP_CASE(2) HOFEM_AP_CASE(3) HOFEM_AP_CASE(4) HOFEM_AP_CASE(5) HOFEM_AP_CASE(6)
+    HOFEM_AP_CASE(7) HOFEM_AP_CASE(8) HOFEM_AP_CASE(9) HOFEM_AP_CASE(10) HOFEM_AP_CASE(11) HOFEM_AP_CASE(12)
+    HOFEM_AP_CASE(13) HOFEM_AP_CASE(14) HOFEM_AP_CASE(15) HOFEM_AP_CASE(16)
+#undef HOFEM_AP_CASE
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

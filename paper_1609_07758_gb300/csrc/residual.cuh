@@ -4,25 +4,40 @@
 
 namespace hofem {
 
+// Folded element tables, sized for the largest order: even part (n/2 + 1)^2, odd part
+// ((n+1)/2)^2, row-major with the order's own row length.
+constexpr int kFoldE = (kMaxN / 2 + 1) * (kMaxN / 2 + 1);
+constexpr int kFoldO = ((kMaxN + 1) / 2) * ((kMaxN + 1) / 2);
+
+// What one sweep computes (all products along the sweep's axis, Q's coefficient is 1):
+//   kApplyFirst: out1 = P x C,  out2 = cA (P x A) + cCP (P x C)
+//   kApplyMid:   out1 = P x C,  out2 = cA (P x A) + cCP (P x C) + Q x C
+//   kApplyLast:                 out2 = [f -] (cA (P x A) + Q x C)
+enum ApplyMode { kApplyFirst = 0, kApplyMid = 1, kApplyLast = 2 };
+
+constexpr int kApplyThreads = 256;
+constexpr int kApplyLines = 32;            // lines per CTA (W)
+
 struct ApplyParams {
   long long outer, inner, outer_per_rhs;   // same geometry as the transform sweeps
   long long tiles_per_outer, seg_per_line, ntiles;
   int M, n, K, W, E;                       // W lines per CTA, E elements per segment
+  int mode;                                // ApplyMode
   const double* P;
-  const double* Q;                         // may be null
-  double* out1;                            // P x C (may be null)
-  double* out2;                            // cA P x A + cCP P x C + cCQ Q x C
-  const double* f;                         // if set: out2 = f - out2
-  double cA, cCP, cCQ;
-  int needPC, needPA;                      // which products of P are used
-  const double* Aloc;                      // (n+1)^2, device (FP64 part of the stiffness)
-  const float* AlocLo;                     // (n+1)^2 remainder of the double-double stiffness
-  const double* Cloc;
-  int threads;
+  const double* Q;                         // kApplyMid, kApplyLast
+  double* out1;                            // kApplyFirst, kApplyMid
+  double* out2;
+  const double* f;                         // kApplyLast, may be null: out2 = f - (...)
+  double cA, cCP;
   size_t smem_bytes;
+  // folded local matrices (centro-symmetry R M R = M), as kernel parameters so that the
+  // unrolled products read them as constant operands
+  double CE[kFoldE], CO[kFoldO];           // mass
+  double AE[kFoldE], AO[kFoldO];           // stiffness (scaled integers for n <= 9, else hi)
+  float AEl[kFoldE], AOl[kFoldO];          // stiffness lo parts (n > 9)
 };
 
-size_t apply_smem_bytes(int n, int W, int E, bool twoInputs);
+size_t apply_smem_bytes(int n, int E);
 cudaError_t apply_set_smem_limits();
 cudaError_t launch_apply(const ApplyParams& p, cudaStream_t s);
 
