@@ -7,6 +7,10 @@ this package only loads it and marshals arguments (see ``binding``).  There is n
 fallback: calls fail with ``HofemError`` when the library cannot be loaded.
 """
 from .binding import (  # noqa: F401
+    HOFEM_BF16,
+    HOFEM_BF16_REFINED,
+    HOFEM_FP16,
+    HOFEM_FP16_REFINED,
     HOFEM_FP32,
     HOFEM_FP32_REFINED,
     HOFEM_FP64,

@@ -12,7 +12,11 @@ _LIB_NAME = "libhofem.so"
 
 HOFEM_FP64 = 0
 HOFEM_FP32 = 1
+HOFEM_BF16 = 2
+HOFEM_FP16 = 3
 HOFEM_FP32_REFINED = 4
+HOFEM_BF16_REFINED = 5
+HOFEM_FP16_REFINED = 6
 
 EXPORTED = (
     "hofem_plan", "hofem_set_refinement", "hofem_reserve", "hofem_solve", "hofem_apply",

@@ -60,7 +60,12 @@ struct hofem_plan_s {
   DevAxis ax[3];
   // workspace
   int ws_nrhs = 0;
-  float* work32 = nullptr;       // low-precision work array
+  float* work32 = nullptr;       // low-precision work array of the forward sweeps (FP32)
+  void* work16 = nullptr;        // BF16 / FP16 plans: work array after the eigenvalue division
+  int wfmt = kFmtF32;            // StoreFmt of the arrays after the division
+  bool refined = false;          // *_REFINED dtype
+  unsigned long long* amax = nullptr;   // per-rhs max |rhs| (FP16 work arrays only)
+  int amax_exp = 10;             // FP16: scaled right-hand sides have |max| in [2^(e-1), 2^e)
   double* r64 = nullptr;         // residual
   double* tmp64[4] = {nullptr, nullptr, nullptr, nullptr};
   double* norms = nullptr;       // 2 per rhs
@@ -156,9 +161,11 @@ void free_axis(DevAxis& a) {
 
 void free_workspace(hofem_plan_s* p) {
   cudaFree(p->work32); p->work32 = nullptr;
+  cudaFree(p->work16); p->work16 = nullptr;
   cudaFree(p->r64); p->r64 = nullptr;
   for (auto& t : p->tmp64) { cudaFree(t); t = nullptr; }
   cudaFree(p->norms); p->norms = nullptr;
+  cudaFree(p->amax); p->amax = nullptr;
   if (p->h_norms) cudaFreeHost(p->h_norms);
   p->h_norms = nullptr;
   p->ws_nrhs = 0;
@@ -174,6 +181,14 @@ hofem_status reserve(hofem_plan_s* p, int nrhs) {
   if (low) {
     HOFEM_CUDA(cudaMalloc(&p->work32, cnt * sizeof(float)), "cudaMalloc(work)");
     bytes += cnt * sizeof(float);
+  }
+  if (p->wfmt != kFmtF32) {
+    HOFEM_CUDA(cudaMalloc(&p->work16, cnt * 2), "cudaMalloc(half work)");
+    bytes += cnt * 2;
+  }
+  if (p->wfmt == kFmtF16) {
+    HOFEM_CUDA(cudaMalloc(&p->amax, (size_t)nrhs * sizeof(unsigned long long)), "cudaMalloc(amax)");
+    bytes += (size_t)nrhs * sizeof(unsigned long long);
   }
   HOFEM_CUDA(cudaMalloc(&p->r64, cnt * sizeof(double)), "cudaMalloc(residual)");
   bytes += cnt * sizeof(double);
@@ -275,9 +290,10 @@ Geo geometry(const hofem_plan_s* p, int axis) {
   return g;
 }
 
-hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void* in, bool in_f64, void* out,
-                       bool out_f64, bool accumulate, double* norms, long long nrhs, cudaStream_t s,
-                       long long lines_override = -1) {
+hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void* in, int in_fmt, void* out,
+                       int out_fmt, bool accumulate, double* norms, long long nrhs, cudaStream_t s,
+                       long long lines_override = -1, const unsigned long long* in_amax = nullptr,
+                       const unsigned long long* out_amax = nullptr) {
   const DevAxis& A = p->ax[axis];
   SweepParams P{};
   Geo g = geometry(p, axis);
@@ -304,9 +320,15 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   P.W = W;
   P.mode = mode;
   P.in = in;
-  P.in_f64 = in_f64;
+  P.in_fmt = in_fmt;
   P.out = out;
-  P.out_f64 = out_f64;
+  P.out_fmt = out_fmt;
+  P.in_amax = in_amax;
+  P.out_amax = out_amax;
+  P.amax_exp = p->amax_exp;
+  // FP16 intermediates carry the eigenvalue-sum prescale between the fused and inverse sweeps
+  P.lscale = !f64 && ((mode == kFwdScaleInv && out_fmt == kFmtF16) || (mode == kInv && in_fmt == kFmtF16));
+  P.lamR = (P.lscale && mode == kInv && axis < p->N - 1) ? (const void*)p->ax[axis + 1].lam32 : nullptr;
   P.accumulate = accumulate;
   P.norms = norms;
   P.mix = f64 ? (const void*)A.mix64 : (const void*)A.mix32;
@@ -350,20 +372,35 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
 }
 
 // One low- or full-precision solve f -> u (algorithm (a)); accumulate: u += solution.
+// Low precision: the forward sweeps keep FP32 intermediates; the fused sweep and the
+// inverse sweeps keep the plan's format (FP32, BF16 or FP16).  Rounding an array that is
+// still physical along some axis spreads its error over every frequency of that axis,
+// where the eigenvalue division amplifies the smooth ones by up to the 1D condition
+// number; after the division rounding errors stay relative.  FP16 adds an exact
+// power-of-two scale of each right-hand side.
 hofem_status solve_once(hofem_plan_s* p, const double* f, double* u, int nrhs, bool f64, bool accumulate,
                         double* norms, cudaStream_t s) {
   hofem_status st;
-  void* work = f64 ? (void*)u : (void*)p->work32;
+  void* wa = f64 ? (void*)u : (void*)p->work32;                                   // before the division
+  void* wb = f64 ? (void*)u : (p->wfmt == kFmtF32 ? (void*)p->work32 : p->work16);  // after it
+  const int fa = f64 ? kFmtF64 : kFmtF32, fb = f64 ? kFmtF64 : p->wfmt;
   if (f64 && accumulate) return fail(HOFEM_ERR_INVALID_ARG, "internal: FP64 solve cannot accumulate");
+  const unsigned long long* amax = nullptr;
+  if (!f64 && p->wfmt == kFmtF16) {
+    HOFEM_CUDA(cudaMemsetAsync(p->amax, 0, (size_t)nrhs * sizeof(unsigned long long), s), "memset amax");
+    HOFEM_CUDA(launch_absmax(f, p->total, nrhs, p->amax, s), "absmax launch");
+    amax = p->amax;
+  }
   const int N = p->N;
   // forward along the contiguous axis, then the strided ones down to axis 1
-  if ((st = run_sweep(p, N - 1, kFwd, f64, f, true, work, f64, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
+  if ((st = run_sweep(p, N - 1, kFwd, f64, f, kFmtF64, wa, fa, false, nullptr, nrhs, s, -1, amax)) != HOFEM_OK)
+    return st;
   for (int a = N - 2; a >= 1; --a)
-    if ((st = run_sweep(p, a, kFwd, f64, work, f64, work, f64, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
-  if ((st = run_sweep(p, 0, kFwdScaleInv, f64, work, f64, work, f64, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
+    if ((st = run_sweep(p, a, kFwd, f64, wa, fa, wa, fa, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
+  if ((st = run_sweep(p, 0, kFwdScaleInv, f64, wa, fa, wb, fb, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
   for (int a = 1; a <= N - 2; ++a)
-    if ((st = run_sweep(p, a, kInv, f64, work, f64, work, f64, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
-  return run_sweep(p, N - 1, kInv, f64, work, f64, u, true, accumulate, norms, nrhs, s);
+    if ((st = run_sweep(p, a, kInv, f64, wb, fb, wb, fb, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
+  return run_sweep(p, N - 1, kInv, f64, wb, fb, u, kFmtF64, accumulate, norms, nrhs, s, -1, nullptr, amax);
 }
 
 // One operator sweep along `axis` (modes in residual.cuh): Q == nullptr is the first
@@ -375,7 +412,7 @@ hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double
   const bool strided = g.inner > 1;
   ApplyParams P{};
   const int W = kApplyLines;
-  int E = 8;
+  int E = 16;   // elements per CTA: measured best of 4 / 8 / 16 at n = 9, K = 1024
   if (const char* env = getenv("HOFEM_APPLY_E")) {
     const int e = atoi(env);
     if (e >= 1 && e <= 256) E = e;
@@ -499,8 +536,7 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
   if (N != 2 && N != 3) return fail(HOFEM_ERR_INVALID_ARG, "N must be 2 or 3");
   if (!K || !X) return fail(HOFEM_ERR_INVALID_ARG, "K or X is NULL");
   if (n < 1 || n > kMaxN) return fail(HOFEM_ERR_INVALID_ARG, "order n must be in 1..16");
-  if (dtype != HOFEM_FP64 && dtype != HOFEM_FP32 && dtype != HOFEM_FP32_REFINED)
-    return fail(HOFEM_ERR_UNSUPPORTED, "dtype not supported");
+  if (dtype < HOFEM_FP64 || dtype > HOFEM_FP16_REFINED) return fail(HOFEM_ERR_UNSUPPORTED, "unknown dtype");
   double lam_bound = 0.0;
   for (int i = 0; i < N; ++i) {
     if (K[i] < 2) return fail(HOFEM_ERR_INVALID_ARG, "K must be >= 2");
@@ -521,7 +557,19 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
   p->N = N;
   p->n = n;
   p->dtype = dtype;
+  p->refined = dtype == HOFEM_FP32_REFINED || dtype == HOFEM_BF16_REFINED || dtype == HOFEM_FP16_REFINED;
+  p->wfmt = (dtype == HOFEM_BF16 || dtype == HOFEM_BF16_REFINED)   ? kFmtBF16
+            : (dtype == HOFEM_FP16 || dtype == HOFEM_FP16_REFINED) ? kFmtF16
+                                                                   : kFmtF32;
   p->alpha = alpha;
+  // FP16 target exponent: high enough that the eigenvalue-damped lines stay above FP16's
+  // smallest normal, with 2^6 headroom below its largest value for the transforms' gain
+  // (measured: 2^12 overflowed at n = 8 in 3D); higher orders keep more headroom
+  p->amax_exp = n <= 9 ? 10 : 6;
+  if (const char* env = getenv("HOFEM_F16_EXP")) {   // tuning knob
+    const int e = atoi(env);
+    if (e >= -4 && e <= 14) p->amax_exp = e;
+  }
   p->total = 1;
   for (int i = 0; i < N; ++i) {
     p->K[i] = K[i];
@@ -566,7 +614,9 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
     delete p;
     return st;
   }
-  p->refine_iters = dtype == HOFEM_FP32_REFINED ? 2 : 0;
+  // default correction steps, measured to reach < 1e-13 for n <= 9 (FP32 2; BF16 and FP16
+  // 4-8 at n = 8-9, K = 64-1024)
+  p->refine_iters = dtype == HOFEM_FP32_REFINED ? 2 : (dtype == HOFEM_BF16_REFINED || dtype == HOFEM_FP16_REFINED) ? 8 : 0;
   hofem_info& inf = p->info;
   inf.N = N;
   inf.n = n;
@@ -585,8 +635,8 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
 
 hofem_status hofem_set_refinement(hofem_plan_t p, int iters, double tol) {
   if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
-  if (p->dtype != HOFEM_FP32_REFINED) return fail(HOFEM_ERR_INVALID_ARG, "plan dtype is not refined");
-  if (iters < 0 || iters > 16 || !(tol >= 0.0)) return fail(HOFEM_ERR_INVALID_ARG, "iters in 0..16, tol >= 0");
+  if (!p->refined) return fail(HOFEM_ERR_INVALID_ARG, "plan dtype is not refined");
+  if (iters < 0 || iters > 100 || !(tol >= 0.0)) return fail(HOFEM_ERR_INVALID_ARG, "iters in 0..100, tol >= 0");
   p->refine_iters = iters;
   p->refine_tol = tol;
   p->info.refine_iters = iters;
@@ -604,7 +654,7 @@ hofem_status hofem_solve(hofem_plan_t p, const double* f, double* u, int nrhs, v
   if (!f || !u) return fail(HOFEM_ERR_INVALID_ARG, "f or u is NULL");
   if (nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "nrhs must be >= 1");
   cudaStream_t s = (cudaStream_t)stream;
-  const bool refined = p->dtype == HOFEM_FP32_REFINED;
+  const bool refined = p->refined;
   if (refined && (const void*)f == (const void*)u)
     return fail(HOFEM_ERR_INVALID_ARG, "f and u must differ for refined solves");
   hofem_status st;
@@ -677,7 +727,7 @@ hofem_status hofem_transform1d(hofem_plan_t p, int axis, int inverse, const doub
   if (!in || !out || lines < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or lines");
   const bool f64 = p->dtype == HOFEM_FP64;
   // work in the output buffer: FP64 in place, or via the FP32 path converting on load/store
-  return run_sweep(p, axis, inverse ? kInv : kFwd, f64, in, true, out, true, false, nullptr, 1,
+  return run_sweep(p, axis, inverse ? kInv : kFwd, f64, in, kFmtF64, out, kFmtF64, false, nullptr, 1,
                    (cudaStream_t)stream, lines);
 }
 

@@ -26,6 +26,9 @@
 // and v_j = (x_j + x_{K-j}) exp(-i pi j / K) (odd outputs), done in shared memory by
 // Stockham autosort passes of radix 2..16 with register butterflies.
 #include <cstdint>
+#include <algorithm>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "sweep.cuh"
 
@@ -765,8 +768,21 @@ __device__ void wfft_dispatch(const Tile<float>& tl, float2* X, int XS, float2* 
   }
 }
 
-template <typename T> __device__ __forceinline__ T ldcvt(const void* p, size_t i, int f64) {
-  return f64 ? (T)__ldg((const double*)p + i) : (T)__ldg((const float*)p + i);
+// load element i of an array in format fmt, times the power of two sc
+template <typename T> __device__ __forceinline__ T ldcvt(const void* p, size_t i, int fmt, double sc) {
+  switch (fmt) {
+    case kFmtF64: return (T)(__ldg((const double*)p + i) * sc);
+    case kFmtBF16: return (T)__bfloat162float(__ldg((const __nv_bfloat16*)p + i)) * (T)sc;
+    case kFmtF16: return (T)__half2float(__ldg((const __half*)p + i)) * (T)sc;
+    default: return (T)__ldg((const float*)p + i) * (T)sc;
+  }
+}
+
+// s with |max| s in [2^(e-1), 2^e), or 1 without a recorded maximum
+__device__ __forceinline__ double amax_scale(const unsigned long long* amax, long long rhs, int e) {
+  if (!amax) return 1.0;
+  const double m = __longlong_as_double((long long)amax[rhs]);
+  return m > 0.0 ? ldexp(1.0, e - ilogb(m) - 1) : 1.0;
 }
 
 template <typename T, bool WF>
@@ -783,6 +799,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
   off += ((size_t)W * kMaxN * sizeof(T) + 15) & ~(size_t)15;
   T* lrest = reinterpret_cast<T*>(smem_raw + off);
   off += ((size_t)W * sizeof(T) + 15) & ~(size_t)15;
+  T* lfac = reinterpret_cast<T*>(smem_raw + off);   // per-line output factor (lscale)
+  off += ((size_t)W * sizeof(T) + 15) & ~(size_t)15;
   double* red = reinterpret_cast<double*>(smem_raw + off);
 
   const Tile<T> tl{tile, P.ps, P.ws};
@@ -793,6 +811,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
   const long long nl = contiguous ? P.outer_per_rhs : P.inner;
   const int wvalid = (int)min((long long)W, nl - l0);
   const long long rhs = contiguous ? o : o / P.outer_per_rhs;
+  const double in_sc = amax_scale(P.in_amax, rhs, P.amax_exp);
+  const double out_sc = P.out_amax ? 1.0 / amax_scale(P.out_amax, rhs, P.amax_exp) : 1.0;
 
   // ---- load: tile element e = (line w, position p) is e = w M + p (contiguous lines) or
   // e = p W + w (strided columns); 8 independent loads per thread are in flight at once.
@@ -811,7 +831,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
       const int e = e0 + u * blockDim.x;
-      v[u] = (e < total && valid(e)) ? ldcvt<T>(P.in, (size_t)gaddr(e), P.in_f64) : (T)0;
+      v[u] = (e < total && valid(e)) ? ldcvt<T>(P.in, (size_t)gaddr(e), P.in_fmt, in_sc) : (T)0;
     }
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
@@ -822,17 +842,34 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
   if (P.mode == kFwdScaleInv) {
     for (int w = threadIdx.x; w < W; w += blockDim.x) {
       const long long c = l0 + w;
-      double lr = P.alpha;
+      double rest = 0.0;
       if (w < wvalid) {
         const long long qa = P.lamB ? c / P.MB : c;
-        lr += (double)((const T*)P.lamA)[qa];
-        if (P.lamB) lr += (double)((const T*)P.lamB)[c - qa * P.MB];
+        rest += (double)((const T*)P.lamA)[qa];
+        if (P.lamB) rest += (double)((const T*)P.lamB)[c - qa * P.MB];
       }
-      lrest[w] = (T)lr;
+      lrest[w] = (T)(P.alpha + rest);
+      lfac[w] = (T)rest;
+    }
+  } else if (P.lscale) {
+    // inverse sweep of prescaled data: this line's share of the eigenvalue sum
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+      const T r = (P.lamR && w < wvalid) ? ((const T*)P.lamR)[l0 + w] : (T)0;
+      lrest[w] = r;
+      lfac[w] = r;
     }
   }
   __syncthreads();
 
+  if (P.lscale && P.mode == kInv) {
+    // undo the prescale of the previous sweep: value / (lambda_axis(q) + rest of the line)
+    const T* lam = (const T*)P.lam;
+    for (int it = threadIdx.x; it < M * W; it += blockDim.x) {
+      const int w = it & (W - 1), q = it >> logW;
+      tl.at(q, w) = tl.at(q, w) / (lam[q] + lrest[w]);
+    }
+    __syncthreads();
+  }
   const T* mix = (const T*)P.mix;
   const T* evec = (const T*)P.evec;
   const C* tw = (const C*)P.tw;
@@ -859,10 +896,19 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
     if (P.mode & kInv) inverse_transform<T>(tl, fbuf, save, W, n, K, P, mix, evec, tw);
   }
 
+  if (P.lscale && P.out_fmt != kFmtF64) {
+    // prescale by the eigenvalue sum of the axes still to invert (one factor per line), so
+    // that coefficients damped by it stay inside the storage format's exponent range
+    for (int it = threadIdx.x; it < M * W; it += blockDim.x) {
+      const int w = it & (W - 1), q = it >> logW;
+      tl.at(q, w) = tl.at(q, w) * lfac[w];
+    }
+    __syncthreads();
+  }
   // ---- store (same element order as the load)
   double s_d = 0.0, s_u = 0.0;
   for (int e0 = threadIdx.x; e0 < total; e0 += UNR * blockDim.x) {
-    if (P.out_f64) {
+    if (P.out_fmt == kFmtF64) {
       double* out = (double*)P.out;
       double prev[UNR];
 #pragma unroll
@@ -874,7 +920,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
       for (int u = 0; u < UNR; ++u) {
         const int e = e0 + u * blockDim.x;
         if (e < total && valid(e)) {
-          const double v = (double)tile[e + (e >> TileSwz<T>::v)];
+          const double v = (double)tile[e + (e >> TileSwz<T>::v)] * out_sc;
           const double r = prev[u] + v;
           out[gaddr(e)] = r;
           s_d += v * v;
@@ -882,11 +928,15 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
         }
       }
     } else {
-      float* out = (float*)P.out;
 #pragma unroll
       for (int u = 0; u < UNR; ++u) {
         const int e = e0 + u * blockDim.x;
-        if (e < total && valid(e)) out[gaddr(e)] = (float)tile[e + (e >> TileSwz<T>::v)];
+        if (e < total && valid(e)) {
+          const float v = (float)tile[e + (e >> TileSwz<T>::v)] * (float)out_sc;
+          if (P.out_fmt == kFmtBF16) ((__nv_bfloat16*)P.out)[gaddr(e)] = __float2bfloat16_rn(v);
+          else if (P.out_fmt == kFmtF16) ((__half*)P.out)[gaddr(e)] = __float2half_rn(v);
+          else ((float*)P.out)[gaddr(e)] = v;
+        }
       }
     }
   }
@@ -914,6 +964,24 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
   }
 }
 
+// Per-rhs max |x| (FP64 bit patterns of non-negative values order like the values).
+__global__ void absmax_kernel(const double* __restrict__ x, long long per_rhs, unsigned long long* amax) {
+  const long long r = blockIdx.y;
+  const double* xr = x + r * per_rhs;
+  double m = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per_rhs; i += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(__ldg(xr + i)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(amax + r, (unsigned long long)__double_as_longlong(m));
+}
+
+cudaError_t launch_absmax(const double* x, long long per_rhs, int nrhs, unsigned long long* amax, cudaStream_t s) {
+  const long long blocks = std::min<long long>((per_rhs + 255) / 256, 4 * 152);
+  absmax_kernel<<<dim3((unsigned)std::max<long long>(blocks, 1), (unsigned)nrhs), 256, 0, s>>>(x, per_rhs, amax);
+  return cudaGetLastError();
+}
+
 int sweep_tile_elems(int M, int W, int tsize) {
   const long long e = (long long)M * W;
   return (int)(e + (e >> (tsize == 4 ? TileSwz<float>::v : TileSwz<double>::v)) + 1);
@@ -935,7 +1003,7 @@ size_t sweep_smem_bytes_fbuf(int M, int W, long long fbuf_complex, int tsize) {
   size_t off = ((size_t)sweep_tile_elems(M, W, tsize) * tsize + 15) & ~(size_t)15;
   off += (size_t)fbuf_complex * 2 * tsize;
   off += ((size_t)W * kMaxN * tsize + 15) & ~(size_t)15;
-  off += ((size_t)W * tsize + 15) & ~(size_t)15;
+  off += 2 * (((size_t)W * tsize + 15) & ~(size_t)15);
   off += 2 * 32 * sizeof(double);
   return off;
 }
@@ -947,7 +1015,7 @@ size_t sweep_smem_bytes(int M, int n, int K, int W, int J, int tsize, bool strid
   const int fs = tsize == 4 ? fft_stride<float>(K) : fft_stride<double>(K);
   off += (size_t)J * 2 * fs * 2 * tsize;
   off += ((size_t)W * kMaxN * tsize + 15) & ~(size_t)15;
-  off += ((size_t)W * tsize + 15) & ~(size_t)15;
+  off += 2 * (((size_t)W * tsize + 15) & ~(size_t)15);
   off += 2 * 32 * sizeof(double);
   return off;
 }

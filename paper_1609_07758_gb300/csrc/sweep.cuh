@@ -18,6 +18,8 @@
 namespace hofem {
 
 enum SweepMode : int { kFwd = 1, kInv = 2, kFwdScaleInv = 3 };
+// storage format of a sweep's input or output array
+enum StoreFmt : int { kFmtF32 = 0, kFmtF64 = 1, kFmtBF16 = 2, kFmtF16 = 3 };
 
 struct SweepParams {
   // geometry of the sweep: lines along one axis of a C-order array
@@ -30,10 +32,22 @@ struct SweepParams {
   int mode;
   // data
   const void* in;
-  int in_f64;
+  int in_fmt;                 // StoreFmt
   void* out;
-  int out_f64;
+  int out_fmt;
   int accumulate;             // out (FP64) += result
+  // optional per-rhs |max| of the original right-hand side (FP64 bit patterns): the input is
+  // multiplied by the power of two s with |max| s in [2^(amax_exp-1), 2^amax_exp) and the
+  // output by 1/s, which keeps FP16 intermediates inside their exponent range (exact)
+  const unsigned long long* in_amax;
+  const unsigned long long* out_amax;
+  int amax_exp;
+  // FP16 intermediates: the fused sweep stores its lines multiplied by the eigenvalue sum
+  // of the other axes; an inverse sweep divides its input by lam(q) + lamR(line) and
+  // multiplies its (non-FP64) output by lamR(line), lamR = eigenvalues of the next axis
+  // by column (null: 0)
+  int lscale;
+  const void* lamR;
   double* norms;              // if non-null: per rhs {sum result^2, sum out_new^2} (atomics)
   // axis tables, in the work precision T
   const void* mix;            // (K-1) n NP, rows padded to NP entries
@@ -74,5 +88,7 @@ long long wfft_fbuf_complex(int W, int n, int K, int nwarps);
 size_t sweep_smem_bytes_fbuf(int M, int W, long long fbuf_complex, int tsize);
 int sweep_max_jobs(int K, int tsize, int threads);
 cudaError_t sweep_set_smem_limits();
+// amax[r] = max |x| over right-hand side r (FP64 bit patterns; amax must be zeroed first)
+cudaError_t launch_absmax(const double* x, long long per_rhs, int nrhs, unsigned long long* amax, cudaStream_t s);
 
 }  // namespace hofem

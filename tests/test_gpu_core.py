@@ -92,10 +92,12 @@ SOLVE_CASES = [
 ]
 
 
-# FP32 + FP64-residual refinement converges to 1e-12 for the practical orders n <= 9;
-# equispaced n >= 12 elements are too ill-conditioned for it (FP64 and FP32 still tested).
-SOLVE_PARAMS = [(dt, tol) + c for c in SOLVE_CASES for dt, tol in ((0, 1e-12), (1, 1e-5), (4, 1e-12))
-                if not (dt == 4 and c[1] > 9)]
+# Low-precision + FP64-residual refinement converges to 1e-12 for the practical orders
+# n <= 9; equispaced n >= 12 elements are too ill-conditioned for it (the unrefined
+# dtypes are still tested).  Unrefined bounds: FP32 1e-5, BF16 / FP16 1e-2.
+DTYPE_TOLS = ((0, 1e-12), (1, 1e-5), (2, 1e-2), (3, 1e-2), (4, 1e-12), (5, 1e-12), (6, 1e-12))
+SOLVE_PARAMS = [(dt, tol) + c for c in SOLVE_CASES for dt, tol in DTYPE_TOLS
+                if not (dt >= 4 and c[1] > 9)]
 
 
 @pytest.mark.parametrize("dtype,tol,N,n,K,X,alpha,nrhs", SOLVE_PARAMS)
@@ -110,6 +112,7 @@ def test_solve_matches_oracle(dtype, tol, N, n, K, X, alpha, nrhs):
     plan.solve(fd, ud, nrhs)
     torch.cuda.synchronize()
     err = rel_l2(ud.cpu().numpy(), ref)
+    print(f"dtype {dtype} N {N} n {n} K {K}: rel L2 {err:.2e}, {plan.info().iterations} steps")
     assert err <= tol, err
     assert np.array_equal(fd.cpu().numpy(), f)          # f is not modified
 
@@ -130,6 +133,26 @@ def test_apply_and_residual_match_oracle(N, n, K, X, alpha, nrhs):
     plan.residual(fd, ud, rd, nrhs)
     torch.cuda.synchronize()
     assert rel_l2(rd.cpu().numpy(), f - ref) <= 1e-13
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1.0, 1e30])
+def test_fp16_solve_scales_each_rhs(scale):
+    """FP16 work arrays: each right-hand side is scaled by a power of two into range."""
+    n, K = 3, [16, 32]
+    Ms = [n * k - 1 for k in K]
+    f = np.random.default_rng(3).standard_normal([2] + Ms)
+    f[1] *= 1e-6                                   # two RHS of very different size
+    f *= scale
+    ref = osolve.solve_tensor(f, [n, n], K, [1.0, 1.0])
+    for dtype, tol in ((H().HOFEM_FP16, 1e-2), (H().HOFEM_FP16_REFINED, 1e-12)):
+        plan = H().Plan(2, K, n, [1.0, 1.0], dtype)
+        fd = dev(f)
+        ud = torch.zeros_like(fd)
+        plan.solve(fd, ud, 2)
+        torch.cuda.synchronize()
+        u = ud.cpu().numpy()
+        for r in range(2):
+            assert rel_l2(u[r], ref[r]) <= tol
 
 
 def test_fp64_solve_in_place():

@@ -2,7 +2,8 @@
 
 2D n = 9, K = 1024 (9215^2 unknowns): FP64 and FP32 + FP64-residual refinement against
 the oracle's dense tensor-product solve, rel. L2 <= 1e-12.  2D n = 2, K = 64 with the
-manufactured sine solution plus noise.  3D n = 4, K = 128 (511^3) refined.
+manufactured sine solution plus noise.  3D n = 4, K = 128 (511^3) refined.  3D n = 8,
+K = 64 (511^3), 16 right-hand sides, BF16 and FP16 work arrays with FP64 refinement.
 """
 import numpy as np
 import pytest
@@ -85,3 +86,29 @@ def test_3d_n4_k128_mixed_matches_oracle():
     err = rel_l2(ud.cpu().numpy(), ref)
     print(f"3D rel L2 vs oracle {err:.3e}")
     assert err <= 1e-12
+
+
+@pytest.mark.parametrize("dtype_name", ["HOFEM_FP16_REFINED", "HOFEM_BF16_REFINED"])
+def test_3d_n8_k64_16rhs_half_refined(dtype_name):
+    """16 RHS at once: every RHS against the FP64 GPU solve, two of them against the oracle."""
+    from paper_1609_07758_gb300 import inputs
+    n, K, nrhs = 8, 64, 16
+    M = n * K - 1
+    f = inputs.gaussian_rhs(5, (nrhs, M, M, M))
+    fd = torch.from_numpy(f).cuda()
+    u64 = torch.zeros_like(fd)
+    p64 = H().Plan(3, [K] * 3, n, [1.0] * 3, H().HOFEM_FP64)
+    p64.solve(fd, u64, nrhs)
+    plan = H().Plan(3, [K] * 3, n, [1.0] * 3, getattr(H(), dtype_name))
+    ud = torch.zeros_like(fd)
+    plan.solve(fd, ud, nrhs)
+    torch.cuda.synchronize()
+    info = plan.info()
+    errs = [float(torch.linalg.vector_norm(ud[r] - u64[r]) / torch.linalg.vector_norm(u64[r])) for r in range(nrhs)]
+    print(f"{dtype_name}: {info.iterations} steps, max rel L2 vs FP64 over 16 RHS {max(errs):.3e}")
+    assert max(errs) <= 1e-12
+    for r in (0, nrhs - 1):
+        ref = osolve.solve_tensor(f[r:r + 1], [n] * 3, [K] * 3, [1.0] * 3)
+        err = rel_l2(ud[r:r + 1].cpu().numpy(), ref)
+        print(f"  rhs {r}: rel L2 vs oracle {err:.3e}")
+        assert err <= 1e-12
