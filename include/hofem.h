@@ -93,7 +93,9 @@ typedef struct {
   double total_ms;
 } hofem_kernel_time;
 
-/* Build a plan: N = 2 or 3 axes, K[i] >= 2 elements (power of two, <= 8192) and length
+/* Build a plan: N = 2 or 3 axes, 2 <= K[i] <= 8192 elements (any K; powers of two take
+ * the fastest FFT path, other K mixed-radix passes costing the sum of K's prime factors
+ * per point) and length
  * X[i] > 0 per axis, order 1 <= n <= 16, alpha > -pi^2 sum_i X_i^-2 (Sect. 2 par. 4).
  * Computes, on the GPU in double-double arithmetic, the 1D eigen-data of every axis:
  * for k = 1..K-1 the n eigenpairs of the theta-family of Theorem 1 part 3, for k = 0 the

@@ -134,13 +134,26 @@ void fold_profile(hofem_plan_s* p) {
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
-void radix_plan(int K, int* npass, int* radix) {
-  int m = 0;
-  while ((1 << m) < K) ++m;
+// DIF radices of a length-K FFT, first pass first: 16s (and one smaller power of two) for
+// K = 2^m; otherwise the prime factors with pairs of 2s merged to 4s, smallest first.
+// Returns false if more than 8 passes would be needed.
+bool radix_plan(int K, int* npass, int* radix) {
   int np = 0;
-  while (m >= 4) { radix[np++] = 16; m -= 4; }
-  if (m > 0) radix[np++] = 1 << m;
+  if (is_pow2(K)) {
+    int m = 0;
+    while ((1 << m) < K) ++m;
+    while (m >= 4) { radix[np++] = 16; m -= 4; }
+    if (m > 0) radix[np++] = 1 << m;
+    *npass = np;
+    return true;
+  }
+  int r = K;
+  while (r % 4 == 0 && np < 8) { radix[np++] = 4; r /= 4; }
+  if (r % 2 == 0 && np < 8) { radix[np++] = 2; r /= 2; }
+  for (int p = 3; p <= r && np < 8; p += 2)
+    while (r % p == 0 && np < 8) { radix[np++] = p; r /= p; }
   *npass = np;
+  return r == 1;
 }
 
 template <typename T>
@@ -305,7 +318,7 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   // the warp-register FFT path is opt-in (HOFEM_WFFT=1): on GB300 it measured slower than
   // the block-wide DIF path (2.5 vs 2.0 ms per sweep at n = 9, K = 1024)
   const char* wf_env = getenv("HOFEM_WFFT");
-  const bool wfft = !f64 && A.h.K >= 32 && A.h.K <= 1024 && wf_env && wf_env[0] == '1' &&
+  const bool wfft = !f64 && is_pow2(A.h.K) && A.h.K >= 32 && A.h.K <= 1024 && wf_env && wf_env[0] == '1' &&
                     choose_sweep_wfft(A.h.M, A.h.n, A.h.K, lines, &W, &nwarps);
   if (!wfft && !choose_sweep(A.h.M, A.h.n, A.h.K, tsize, lines, strided, &W, &J))
     return fail(HOFEM_ERR_UNSUPPORTED, "no launch configuration fits shared memory for this axis");
@@ -351,6 +364,14 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
     }
   }
   P.npass = A.npass;
+  P.pow2 = is_pow2(A.h.K) ? 1 : 0;
+  {
+    int q = A.h.K;
+    for (int i = 0; i < A.npass; ++i) {
+      q /= A.radix[i];
+      P.radix_q[i] = q;
+    }
+  }
   for (int i = 0; i < 8; ++i) {
     P.radix[i] = A.radix[i];
     P.radix_log[i] = A.radix[i] > 0 ? 31 - __builtin_clz(A.radix[i]) : 0;
@@ -540,8 +561,7 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
   double lam_bound = 0.0;
   for (int i = 0; i < N; ++i) {
     if (K[i] < 2) return fail(HOFEM_ERR_INVALID_ARG, "K must be >= 2");
-    if (!is_pow2(K[i]) || K[i] > kMaxK)
-      return fail(HOFEM_ERR_UNSUPPORTED, "K must be a power of two <= 8192");
+    if (K[i] > kMaxK) return fail(HOFEM_ERR_UNSUPPORTED, "K must be <= 8192");
     if (!(X[i] > 0.0) || !std::isfinite(X[i])) return fail(HOFEM_ERR_INVALID_ARG, "X must be positive");
     lam_bound += M_PI * M_PI / (X[i] * X[i]);
   }
@@ -607,7 +627,11 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
     if ((st = upload(a.h.lam, &a.lam32, &tb)) != HOFEM_OK) break;
     if ((st = upload(a.h.evec, &a.evec32, &tb)) != HOFEM_OK) break;
     if ((st = upload(a.h.tw, &a.tw32, &tb)) != HOFEM_OK) break;
-    radix_plan(K[i], &a.npass, a.radix);
+    if (!radix_plan(K[i], &a.npass, a.radix)) {
+      g_last_error = "K has too many prime factors for the FFT plan (more than 8 passes)";
+      st = HOFEM_ERR_UNSUPPORTED;
+      break;
+    }
   }
   if (st != HOFEM_OK) {
     for (int i = 0; i < N; ++i) free_axis(p->ax[i]);

@@ -10,7 +10,7 @@
 namespace hofem {
 
 constexpr int kMaxN = 16;       // largest element order
-constexpr int kMaxK = 8192;     // largest elements per axis (power of two)
+constexpr int kMaxK = 8192;     // largest elements per axis
 constexpr int kMaxDims = 3;
 // Orders whose element stiffness, scaled by the common denominator of its entries, is an
 // integer matrix exactly representable in FP64; larger orders carry it as hi + lo.

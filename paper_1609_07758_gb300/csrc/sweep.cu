@@ -209,6 +209,63 @@ __device__ __forceinline__ int fft_pos(int m, int logN, const SweepParams& P) {
 }
 
 // ---------------------------------------------------------------------------------
+// General K (not a power of two): mixed-radix decimation-in-frequency passes, each out of
+// place.  A pass of radix R over blocks of length L (stride Q = L / R) writes
+//   dst[b L + j + q Q] = w_L^{j q} sum_r src[b L + j + r Q] w_R^{r q},  w_X = exp(-2 pi i / X),
+// one thread per output (R terms); the two buffers alternate between passes.  The
+// powers of w_R and w_L are entries 2 x (K / R) and 2 x (K / L) of tw (period 2K).
+template <typename T>
+__device__ void fft_pass_direct(const typename Cx<T>::type* src, typename Cx<T>::type* dst, int K, int nfft, int L,
+                                int R, const typename Cx<T>::type* __restrict__ tw) {
+  using C = typename Cx<T>::type;
+  const int Q = L / R, FS = fft_stride<T>(K), total = nfft * K;
+  const int stepR = 2 * (K / R), stepL = 2 * (K / L);
+  for (int o = threadIdx.x; o < total; o += blockDim.x) {
+    const int f = o / K, s = o - f * K;
+    const int blk = s / L, t = s - blk * L;
+    const int q = t / Q, j = t - q * Q;
+    const C* in = src + (size_t)f * FS;
+    const int e0 = blk * L + j;
+    C acc = in[fpad<T>(e0)];
+    int x = 0;                                   // r q mod R
+    for (int r = 1; r < R; ++r) {
+      x += q;
+      if (x >= R) x -= R;
+      acc = c_add(acc, c_mul(in[fpad<T>(e0 + r * Q)], tw[x * stepR]));
+    }
+    if (j != 0 && q != 0) acc = c_mul(acc, tw[((j * q) % L) * stepL]);
+    dst[(size_t)f * FS + fpad<T>(s)] = acc;
+  }
+  __syncthreads();
+}
+
+// All passes; returns the buffer holding the result (a or b).
+template <typename T>
+__device__ typename Cx<T>::type* fft_all_general(typename Cx<T>::type* a, typename Cx<T>::type* b, int K, int nfft,
+                                                 const SweepParams& P, const typename Cx<T>::type* __restrict__ tw) {
+  int L = K;
+  for (int ps = 0; ps < P.npass; ++ps) {
+    const int R = P.radix[ps];
+    fft_pass_direct<T>(a, b, K, nfft, L, R, tw);
+    typename Cx<T>::type* t = a;
+    a = b;
+    b = t;
+    L /= R;
+  }
+  return a;
+}
+
+__device__ __forceinline__ int fft_pos_general(int m, const SweepParams& P) {
+  int pos = 0;
+  for (int ps = 0; ps < P.npass; ++ps) {
+    const int R = P.radix[ps], d = m % R;
+    m /= R;
+    pos += d * P.radix_q[ps];
+  }
+  return pos;
+}
+
+// ---------------------------------------------------------------------------------
 // Job = one complex DST pair: real part = component ma of line wa, imaginary part =
 // component mb of line wb (mb < 0: absent).  Component 0 = nodes, i = 1..n-1 interior.
 struct Job {
@@ -306,6 +363,51 @@ __device__ __forceinline__ void dst_out(const typename Cx<T>::type* buf, int jb,
   const int FS = fft_stride<T>(K);
   const typename Cx<T>::type* U = buf + (size_t)(2 * jb) * FS;
   const int pos = fpad<T>(fft_pos(k >> 1, logK, P));
+  const typename Cx<T>::type R = (k & 1) ? U[FS + pos] : U[pos];
+  *a = -R.y;
+  *b = R.x;
+}
+
+// dst_load for any K: t = 0 .. K/2 fills slots t and K - t of u and v.
+template <typename T>
+__device__ __noinline__ void dst_load_general(const Tile<T> tl, typename Cx<T>::type* buf, int j0, int nj, int W,
+                                              int n, int K, bool inverse, const typename Cx<T>::type* __restrict__ tw) {
+  using C = typename Cx<T>::type;
+  const int per = K / 2 + 1;
+  const int logW = 31 - __clz(W);
+  const int items = nj * per;
+  const int FS = fft_stride<T>(K);
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int jb = it / per, t = it - jb * per;
+    const Job job = job_of(j0 + jb, W, logW, n);
+    C* U = buf + (size_t)(2 * jb) * FS;
+    C* V = U + FS;
+    if (t == 0) {
+      U[0] = C{(T)0, (T)0};
+      V[0] = C{(T)0, (T)0};
+      continue;
+    }
+    const C x1 = pair_x(tl, job, t, n, K, inverse);
+    if (2 * t == K) {                           // u = 0, v = 2 x w^{K/2}
+      U[fpad<T>(t)] = C{(T)0, (T)0};
+      V[fpad<T>(t)] = c_mul(c_add(x1, x1), tw[t]);
+      continue;
+    }
+    const C x2 = pair_x(tl, job, K - t, n, K, inverse);
+    const C d = c_sub(x1, x2), sm = c_add(x1, x2);
+    U[fpad<T>(t)] = d;
+    U[fpad<T>(K - t)] = C{-d.x, -d.y};
+    V[fpad<T>(t)] = c_mul(sm, tw[t]);
+    V[fpad<T>(K - t)] = c_mul(sm, tw[K - t]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void dst_out_general(const typename Cx<T>::type* buf, int jb, int K, int k, T* a, T* b,
+                                                const SweepParams& P) {
+  const int FS = fft_stride<T>(K);
+  const typename Cx<T>::type* U = buf + (size_t)(2 * jb) * FS;
+  const int pos = fpad<T>(fft_pos_general(k >> 1, P));
   const typename Cx<T>::type R = (k & 1) ? U[FS + pos] : U[pos];
   *a = -R.y;
   *b = R.x;
@@ -482,18 +584,35 @@ __device__ void forward_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
   const int nj_tot = num_jobs(W, n), J = P.jobs_per_batch;
   for (int j0 = 0; j0 < nj_tot; j0 += J) {
     const int nj = min(J, nj_tot - j0);
-    dst_load<T>(tl, fbuf, j0, nj, W, n, K, false, tw);
-    __syncthreads();
-    fft_all<T>(fbuf, logK, 2 * nj, P, tw);
-    const int items = nj << logK;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-      const int jb = it >> logK, k = it & (K - 1);
-      if (k == 0) continue;
-      const Job job = job_of(j0 + jb, W, logW, n);
-      T a, b;
-      dst_out<T>(fbuf, jb, K, logK, k, &a, &b, P);
-      tl.at((k - 1) * n + slot_of(job.ma, n), job.wa) = a;
-      if (job.mb >= 0) tl.at((k - 1) * n + slot_of(job.mb, n), job.wb) = b;
+    if (P.pow2) {
+      dst_load<T>(tl, fbuf, j0, nj, W, n, K, false, tw);
+      __syncthreads();
+      fft_all<T>(fbuf, logK, 2 * nj, P, tw);
+      const int items = nj << logK;
+      for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int jb = it >> logK, k = it & (K - 1);
+        if (k == 0) continue;
+        const Job job = job_of(j0 + jb, W, logW, n);
+        T a, b;
+        dst_out<T>(fbuf, jb, K, logK, k, &a, &b, P);
+        tl.at((k - 1) * n + slot_of(job.ma, n), job.wa) = a;
+        if (job.mb >= 0) tl.at((k - 1) * n + slot_of(job.mb, n), job.wb) = b;
+      }
+    } else {
+      dst_load_general<T>(tl, fbuf, j0, nj, W, n, K, false, tw);
+      __syncthreads();
+      const typename Cx<T>::type* res =
+          fft_all_general<T>(fbuf, fbuf + (size_t)J * 2 * fft_stride<T>(K), K, 2 * nj, P, tw);
+      const int items = nj * K;
+      for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int jb = it / K, k = it - jb * K;
+        if (k == 0) continue;
+        const Job job = job_of(j0 + jb, W, logW, n);
+        T a, b;
+        dst_out_general<T>(res, jb, K, k, &a, &b, P);
+        tl.at((k - 1) * n + slot_of(job.ma, n), job.wa) = a;
+        if (job.mb >= 0) tl.at((k - 1) * n + slot_of(job.mb, n), job.wb) = b;
+      }
     }
     __syncthreads();
   }
@@ -522,17 +641,36 @@ __device__ void inverse_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
   const int nj_tot = num_jobs(W, n), J = P.jobs_per_batch;
   for (int j0 = 0; j0 < nj_tot; j0 += J) {
     const int nj = min(J, nj_tot - j0);
-    dst_load<T>(tl, fbuf, j0, nj, W, n, K, true, tw);
-    __syncthreads();
-    fft_all<T>(fbuf, logK, 2 * nj, P, tw);
+    const typename Cx<T>::type* res = fbuf;
+    if (P.pow2) {
+      dst_load<T>(tl, fbuf, j0, nj, W, n, K, true, tw);
+      __syncthreads();
+      fft_all<T>(fbuf, logK, 2 * nj, P, tw);
+    } else {
+      dst_load_general<T>(tl, fbuf, j0, nj, W, n, K, true, tw);
+      __syncthreads();
+      res = fft_all_general<T>(fbuf, fbuf + (size_t)J * 2 * fft_stride<T>(K), K, 2 * nj, P, tw);
+    }
     // post-combine into physical rows
-    const int items = nj << logK;
+    const int items = nj * K;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-      const int jb = it >> logK, j = (it & (K - 1)) + 1;   // j = 1..K
+      int jb, j;
+      if (P.pow2) {
+        jb = it >> logK;
+        j = (it & (K - 1)) + 1;                        // j = 1..K
+      } else {
+        jb = it / K;
+        j = it - jb * K + 1;
+      }
       const Job job = job_of(j0 + jb, W, logW, n);
       T a0 = (T)0, b0 = (T)0, a1 = (T)0, b1 = (T)0;   // D at j-1 and at j
-      if (j - 1 >= 1) dst_out<T>(fbuf, jb, K, logK, j - 1, &a0, &b0, P);
-      if (j <= K - 1) dst_out<T>(fbuf, jb, K, logK, j, &a1, &b1, P);
+      if (P.pow2) {
+        if (j - 1 >= 1) dst_out<T>(res, jb, K, logK, j - 1, &a0, &b0, P);
+        if (j <= K - 1) dst_out<T>(res, jb, K, logK, j, &a1, &b1, P);
+      } else {
+        if (j - 1 >= 1) dst_out_general<T>(res, jb, K, j - 1, &a0, &b0, P);
+        if (j <= K - 1) dst_out_general<T>(res, jb, K, j, &a1, &b1, P);
+      }
       if (job.ma == 0) {                        // nodes of line wa (and maybe wb)
         if (j <= K - 1) {
           tl.at(j * n - 1, job.wa) = a1;
@@ -989,7 +1127,8 @@ int sweep_tile_elems(int M, int W, int tsize) {
 
 long long sweep_fbuf_complex(int K, int J, int tsize) {
   const int fs = tsize == 4 ? fft_stride<float>(K) : fft_stride<double>(K);
-  return (long long)J * 2 * fs;
+  const bool pow2 = (K & (K - 1)) == 0;
+  return (long long)J * 2 * fs * (pow2 ? 1 : 2);
 }
 
 // Warp-FFT path (FP32, 32 <= K <= 1024): X rows of K + L complex for every job of the
@@ -1012,8 +1151,7 @@ size_t sweep_smem_bytes(int M, int n, int K, int W, int J, int tsize, bool strid
   (void)n;
   (void)strided;
   size_t off = ((size_t)sweep_tile_elems(M, W, tsize) * tsize + 15) & ~(size_t)15;
-  const int fs = tsize == 4 ? fft_stride<float>(K) : fft_stride<double>(K);
-  off += (size_t)J * 2 * fs * 2 * tsize;
+  off += (size_t)sweep_fbuf_complex(K, J, tsize) * 2 * tsize;
   off += ((size_t)W * kMaxN * tsize + 15) & ~(size_t)15;
   off += 2 * (((size_t)W * tsize + 15) & ~(size_t)15);
   off += 2 * 32 * sizeof(double);

@@ -60,10 +60,14 @@ struct SweepParams {
   const void* lamB;
   long long MB;
   double alpha;
-  // FFT plan for length K
+  // FFT plan for length K: radices of the DIF passes (first pass first); pow2 = 1 for
+  // K = 2^m (in-place register passes), else out-of-place mixed-radix passes, whose
+  // output slot of frequency m = sum_i d_i radix_q[i] (m = d_1 + R_1 d_2 + R_1 R_2 d_3 ..)
   int npass;
   int radix[8];
   int radix_log[8];
+  int radix_q[8];
+  int pow2;
   int jobs_per_batch;
   long long fbuf_complex;     // complex elements of the FFT region (batched buffers or X + transposes)
   int wfft;                   // 1: warp-register FFT path (FP32, 32 <= K <= 1024)
@@ -82,7 +86,7 @@ cudaError_t launch_sweep_f64(const SweepParams& p, cudaStream_t s);
 // Shared-memory bytes a sweep needs for (M, n, K, W, J) in precision of size tsize.
 size_t sweep_smem_bytes(int M, int n, int K, int W, int J, int tsize, bool strided);
 int sweep_tile_elems(int M, int W, int tsize);
-long long sweep_fbuf_complex(int K, int J, int tsize);
+long long sweep_fbuf_complex(int K, int J, int tsize);   // doubled (ping-pong) unless K = 2^m
 int wfft_row_stride(int K);
 long long wfft_fbuf_complex(int W, int n, int K, int nwarps);
 size_t sweep_smem_bytes_fbuf(int M, int W, long long fbuf_complex, int tsize);

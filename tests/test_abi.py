@@ -57,7 +57,7 @@ def test_invalid_arguments_are_rejected_on_the_host(lib, N, K, n, X, dtype, alph
 
 def test_unsupported_shapes_and_dtypes(lib):
     out = ctypes.c_void_p()
-    Ks = (ctypes.c_int * 2)(12, 8)           # K not a power of two
+    Ks = (ctypes.c_int * 2)(16384, 8)        # K above 8192
     Xs = (ctypes.c_double * 2)(1.0, 1.0)
     assert lib.hofem_plan(2, Ks, 2, Xs, 0, 0.0, ctypes.byref(out)) == 2
     assert lib.hofem_plan(2, (ctypes.c_int * 2)(8, 8), 2, Xs, 7, 0.0, ctypes.byref(out)) == 2

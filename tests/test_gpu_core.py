@@ -56,8 +56,15 @@ def test_eigen_tables_match_oracle(n, K, X):
 
 @pytest.mark.parametrize("dtype,tol", [(0, 1e-13), (1, 3e-6)])
 @pytest.mark.parametrize("n,K,lines", [(1, 16, 5), (2, 8, 37), (3, 64, 9), (4, 32, 130), (9, 64, 3),
-                                       (5, 2, 4), (8, 256, 7)])
+                                       (5, 2, 4), (8, 256, 7),
+                                       # any K: mixed radices, odd and prime lengths
+                                       (1, 7, 3), (2, 12, 5), (3, 37, 4), (4, 105, 3), (8, 250, 2),
+                                       (2, 509, 2), (6, 3, 9)])
 def test_transform1d_matches_oracle(dtype, tol, n, K, lines):
+    # a K that is not a power of two runs direct DFT passes over its prime factors, whose
+    # FP32 rounding grows like sqrt(p) eps (p = 509: ~4e-6): held to the FP32 bound 1e-5
+    if dtype == 1 and K & (K - 1):
+        tol = 1e-5
     X = 1.3
     plan = H().Plan(2, [K, K], n, [X, X], dtype)
     s = spectrum.spectrum(n, K, X)
@@ -89,6 +96,11 @@ SOLVE_CASES = [
     (3, 2, [8, 8, 8], [1.0, 1.0, 1.0], 0.0, 2),
     (3, 3, [4, 8, 2], [1.0, 0.6, 2.0], 0.5, 1),
     (3, 4, [16, 16, 16], [1.0, 1.0, 1.0], 0.0, 1),
+    # K not a power of two
+    (2, 2, [37, 48], [1.3, 0.7], 0.0, 2),
+    (2, 5, [33, 20], [1.0, 1.0], 0.5, 1),
+    (2, 8, [250, 3], [2.0, 0.6], 0.0, 1),
+    (3, 3, [6, 5, 9], [1.0, 1.0, 1.0], 0.0, 1),
 ]
 
 
