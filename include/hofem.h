@@ -83,7 +83,32 @@ typedef struct {
   int lines_per_cta[3];     /* launch configuration chosen per axis (W) */
   int threads_per_cta;
   long long kernel_launches; /* kernels this plan has launched since it was created */
+  long long tuned_shapes;   /* launch-shape candidates measured by hofem_autotune */
 } hofem_info;
+
+/* One problem of a batch: N = 2 or 3 axes with K[i] elements of length X[i] (entries
+ * i >= N are ignored), order n, alpha, and nrhs right-hand sides (same rules as
+ * hofem_plan). */
+typedef struct {
+  int N;
+  int K[3];
+  int n;
+  double X[3];
+  double alpha;
+  int nrhs;
+} hofem_problem;
+
+typedef struct {
+  int count;                /* problems */
+  int streams;              /* parallel branches of the captured solve graph */
+  long long unknowns;       /* sum over problems of nrhs x prod_i M_i */
+  long long graph_nodes;    /* nodes of the captured solve graph (0 before the first solve) */
+  int captures;             /* times the solve graph was captured */
+  double plan_ms;           /* host wall time of hofem_batch_plan */
+  double tune_ms;           /* host wall time of hofem_batch_tune (0 if not tuned) */
+  size_t table_bytes;       /* device bytes of all eigen / twiddle tables */
+  size_t workspace_bytes;   /* device bytes of all solve workspaces */
+} hofem_batch_info;
 
 /* Per-kernel-kind device time, from CUDA events recorded on the launching stream around
  * every kernel while profiling is enabled (see hofem_profile). */
@@ -104,9 +129,16 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
                         hofem_plan_t* out);
 
 /* Refined dtypes only: iters = residual/correction steps after the first low-precision
- * solve (0..100; default FP32 2, BF16 and FP16 8); tol > 0 additionally stops early once ||delta||/||u|| <= tol,
+ * solve (0..100; default FP32 2 when every K is a power of two, else 3; BF16 and FP16 8); tol > 0 additionally stops early once ||delta||/||u|| <= tol,
  * which synchronises the stream once per step.  tol = 0 keeps a fixed count (capturable). */
 hofem_status hofem_set_refinement(hofem_plan_t plan, int iters, double tol);
+
+/* Autotuner: time every candidate launch shape (sweep lines per CTA W and DST batch J;
+ * operator elements per CTA E) of this plan's solve and apply for nrhs right-hand sides
+ * on its own workspace, and keep the fastest per shape in a process-wide table that
+ * later launches of any plan consult (written to / read from the file named by the
+ * environment variable HOFEM_TUNE_CACHE when set).  Synchronous; reserves workspace. */
+hofem_status hofem_autotune(hofem_plan_t plan, int nrhs, void* stream);
 
 /* Reserve workspace for nrhs right-hand sides (solve allocates on demand otherwise;
  * call this before capturing a solve in a CUDA graph). */
@@ -166,6 +198,29 @@ hofem_status hofem_profile(hofem_plan_t plan, int enable);
  * last hofem_profile call; *count receives the number of kinds.  out is a HOST array. */
 hofem_status hofem_get_profile(hofem_plan_t plan, hofem_kernel_time* out, int max_entries, int* count);
 void hofem_destroy(hofem_plan_t plan);
+
+/* Batched solves of independent problems of uneven K, n, X and nrhs (the benchmark spec's
+ * batch scheduler): one plan per problem with its workspace reserved up front.  The
+ * first hofem_batch_solve captures every problem's solve (the refined dtypes with their
+ * fixed step count) into one CUDA graph whose branches spread the problems over up to 16
+ * streams, so independent problems run concurrently; later calls with the same pointer
+ * arrays relaunch that graph (other pointers recapture it).  Synchronous plan; errors of
+ * one problem name its index in hofem_last_error. */
+hofem_status hofem_batch_plan(int count, const hofem_problem* probs, int dtype, hofem_batch_t* out);
+
+/* hofem_autotune for every problem (shapes shared between problems are measured once). */
+hofem_status hofem_batch_tune(hofem_batch_t batch, void* stream);
+
+/* u_i = A_i^{-1} f_i for every problem i.  f, u: HOST arrays of count device pointers,
+ * each an FP64 array (nrhs_i, M_1..M_N) as for hofem_solve (f_i != u_i).  Asynchronous
+ * on stream: one graph launch. */
+hofem_status hofem_batch_solve(hofem_batch_t batch, const double* const* f, double* const* u, void* stream);
+
+hofem_status hofem_batch_get_info(hofem_batch_t batch, hofem_batch_info* out);
+
+/* The plan of problem i (owned by the batch; for hofem_get_info / hofem_apply). */
+hofem_status hofem_batch_get_plan(hofem_batch_t batch, int i, hofem_plan_t* out);
+void hofem_batch_destroy(hofem_batch_t batch);
 
 const char* hofem_status_string(int status);
 const char* hofem_last_error(void);

@@ -14,10 +14,12 @@ from .binding import (  # noqa: F401
     HOFEM_FP32,
     HOFEM_FP32_REFINED,
     HOFEM_FP64,
+    Batch,
     HofemError,
     Plan,
     hofem_apply,
     hofem_apply_static,
+    hofem_autotune,
     hofem_destroy,
     hofem_get_eigen,
     hofem_get_info,

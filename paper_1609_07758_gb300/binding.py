@@ -22,7 +22,8 @@ EXPORTED = (
     "hofem_plan", "hofem_set_refinement", "hofem_reserve", "hofem_solve", "hofem_apply",
     "hofem_residual", "hofem_transform1d", "hofem_get_eigen", "hofem_get_info",
     "hofem_destroy", "hofem_status_string", "hofem_last_error", "hofem_profile", "hofem_get_profile",
-    "hofem_apply_static",
+    "hofem_apply_static", "hofem_autotune", "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve",
+    "hofem_batch_get_info", "hofem_batch_get_plan", "hofem_batch_destroy",
 )
 
 
@@ -39,8 +40,19 @@ class hofem_info(ctypes.Structure):
         ("converged", ctypes.c_int), ("last_rel_update", ctypes.c_double), ("plan_ms", ctypes.c_double),
         ("table_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
         ("lines_per_cta", ctypes.c_int * 3), ("threads_per_cta", ctypes.c_int),
-        ("kernel_launches", ctypes.c_longlong),
+        ("kernel_launches", ctypes.c_longlong), ("tuned_shapes", ctypes.c_longlong),
     ]
+
+
+class hofem_problem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("K", ctypes.c_int * 3), ("n", ctypes.c_int), ("X", ctypes.c_double * 3),
+                ("alpha", ctypes.c_double), ("nrhs", ctypes.c_int)]
+
+
+class hofem_batch_info(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("streams", ctypes.c_int), ("unknowns", ctypes.c_longlong),
+                ("graph_nodes", ctypes.c_longlong), ("captures", ctypes.c_int), ("plan_ms", ctypes.c_double),
+                ("tune_ms", ctypes.c_double), ("table_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t)]
 
 
 class hofem_kernel_time(ctypes.Structure):
@@ -82,9 +94,19 @@ def load_library():
     lib.hofem_status_string.restype = ctypes.c_char_p
     lib.hofem_last_error.argtypes = []
     lib.hofem_last_error.restype = ctypes.c_char_p
+    lib.hofem_autotune.argtypes = [P, I, V]
+    lib.hofem_batch_plan.argtypes = [I, ctypes.POINTER(hofem_problem), I, ctypes.POINTER(P)]
+    lib.hofem_batch_tune.argtypes = [P, V]
+    lib.hofem_batch_solve.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), V]
+    lib.hofem_batch_get_info.argtypes = [P, ctypes.POINTER(hofem_batch_info)]
+    lib.hofem_batch_get_plan.argtypes = [P, I, ctypes.POINTER(P)]
+    lib.hofem_batch_destroy.argtypes = [P]
+    lib.hofem_batch_destroy.restype = None
     for name in ("hofem_plan", "hofem_set_refinement", "hofem_reserve", "hofem_solve", "hofem_apply",
                  "hofem_residual", "hofem_transform1d", "hofem_get_eigen", "hofem_get_info",
-                 "hofem_profile", "hofem_get_profile", "hofem_apply_static"):
+                 "hofem_profile", "hofem_get_profile", "hofem_apply_static", "hofem_autotune",
+                 "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve", "hofem_batch_get_info",
+                 "hofem_batch_get_plan"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -209,6 +231,10 @@ def hofem_destroy(plan):
         load_library().hofem_destroy(plan)
 
 
+def hofem_autotune(plan, nrhs, stream=None):
+    _check(load_library().hofem_autotune(plan, int(nrhs), _stream(stream)), "hofem_autotune")
+
+
 class Plan:
     """Owns a hofem plan handle (destroyed with the object)."""
 
@@ -238,6 +264,9 @@ class Plan:
     def info(self):
         return hofem_get_info(self.handle)
 
+    def autotune(self, nrhs, stream=None):
+        hofem_autotune(self.handle, nrhs, stream)
+
     def profile(self, enable):
         hofem_profile(self.handle, enable)
 
@@ -250,6 +279,58 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             hofem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owns a hofem batch: problems = list of dicts with keys N, K, n, X, alpha, nrhs."""
+
+    def __init__(self, problems, dtype=HOFEM_FP32_REFINED):
+        lib = load_library()
+        arr = (hofem_problem * len(problems))()
+        for i, q in enumerate(problems):
+            arr[i].N = int(q["N"])
+            for a in range(int(q["N"])):
+                arr[i].K[a] = int(q["K"][a])
+                arr[i].X[a] = float(q["X"][a])
+            arr[i].n = int(q["n"])
+            arr[i].alpha = float(q.get("alpha", 0.0))
+            arr[i].nrhs = int(q.get("nrhs", 1))
+        out = ctypes.c_void_p()
+        _check(lib.hofem_batch_plan(len(problems), arr, int(dtype), ctypes.byref(out)), "hofem_batch_plan")
+        self.handle = out
+        self.count = len(problems)
+
+    def tune(self, stream=None):
+        _check(load_library().hofem_batch_tune(self.handle, _stream(stream)), "hofem_batch_tune")
+
+    def solve(self, fs, us, stream=None):
+        """fs, us: sequences of device FP64 tensors (one per problem)."""
+        if len(fs) != self.count or len(us) != self.count:
+            raise HofemError(1, "Batch.solve", "one f and one u per problem")
+        F = (ctypes.c_void_p * self.count)(*[_ptr(x) for x in fs])
+        U = (ctypes.c_void_p * self.count)(*[_ptr(x) for x in us])
+        _check(load_library().hofem_batch_solve(self.handle, F, U, _stream(stream)), "hofem_batch_solve")
+
+    def info(self):
+        inf = hofem_batch_info()
+        _check(load_library().hofem_batch_get_info(self.handle, ctypes.byref(inf)), "hofem_batch_get_info")
+        return inf
+
+    def plan_info(self, i):
+        p = ctypes.c_void_p()
+        _check(load_library().hofem_batch_get_plan(self.handle, int(i), ctypes.byref(p)), "hofem_batch_get_plan")
+        return hofem_get_info(p)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().hofem_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -8,7 +8,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -303,6 +306,36 @@ Geo geometry(const hofem_plan_s* p, int axis) {
   return g;
 }
 
+// ---- measured launch shapes (autotuner): sweep (W, J) and operator E per shape.
+// key: kind (0 sweep, 1 operator), M, n, K, element bytes, strided, mode, lines
+typedef std::tuple<int, int, int, int, int, int, int, long long> TuneKey;
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tuned;
+bool g_tune_loaded = false;
+thread_local int g_force_a = 0, g_force_b = 0;   // candidate under measurement (0: none)
+
+bool tuned_lookup(const TuneKey& k, int* a, int* b) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(k);
+  if (it == g_tuned.end()) return false;
+  *a = it->second.first;
+  *b = it->second.second;
+  return true;
+}
+
+TuneKey sweep_key(const hofem_plan_s* p, int axis, int mode, bool f64, long long nrhs, long long lines_override) {
+  const DevAxis& A = p->ax[axis];
+  Geo g = geometry(p, axis);
+  if (lines_override >= 0) g = Geo{lines_override, 1};
+  return TuneKey{0, A.h.M, A.h.n, A.h.K, f64 ? 8 : 4, g.inner > 1 ? 1 : 0, mode, nrhs * g.outer_per_rhs * g.inner};
+}
+
+TuneKey apply_key(const hofem_plan_s* p, int axis, int mode, long long nrhs) {
+  const DevAxis& A = p->ax[axis];
+  const Geo g = geometry(p, axis);
+  return TuneKey{1, A.h.M, A.h.n, A.h.K, 8, g.inner > 1 ? 1 : 0, mode, nrhs * g.outer_per_rhs * g.inner};
+}
+
 hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void* in, int in_fmt, void* out,
                        int out_fmt, bool accumulate, double* norms, long long nrhs, cudaStream_t s,
                        long long lines_override = -1, const unsigned long long* in_amax = nullptr,
@@ -320,8 +353,14 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   const char* wf_env = getenv("HOFEM_WFFT");
   const bool wfft = !f64 && is_pow2(A.h.K) && A.h.K >= 32 && A.h.K <= 1024 && wf_env && wf_env[0] == '1' &&
                     choose_sweep_wfft(A.h.M, A.h.n, A.h.K, lines, &W, &nwarps);
-  if (!wfft && !choose_sweep(A.h.M, A.h.n, A.h.K, tsize, lines, strided, &W, &J))
+  const TuneKey key = sweep_key(p, axis, mode, f64, nrhs, lines_override);
+  if (wfft) {
+  } else if (g_force_a > 0) {
+    W = g_force_a;
+    J = g_force_b;
+  } else if (!tuned_lookup(key, &W, &J) && !choose_sweep(A.h.M, A.h.n, A.h.K, tsize, lines, strided, &W, &J)) {
     return fail(HOFEM_ERR_UNSUPPORTED, "no launch configuration fits shared memory for this axis");
+  }
   P.outer = nrhs * g.outer_per_rhs;
   P.inner = g.inner;
   P.outer_per_rhs = g.outer_per_rhs;
@@ -434,6 +473,12 @@ hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double
   ApplyParams P{};
   const int W = kApplyLines;
   int E = 16;   // elements per CTA: measured best of 4 / 8 / 16 at n = 9, K = 1024
+  {
+    int tE = 0, unused = 0;
+    const TuneKey key = apply_key(p, axis, Q_ == nullptr ? kApplyFirst : (out1 ? kApplyMid : kApplyLast), nrhs);
+    if (g_force_a > 0) E = g_force_a;
+    else if (tuned_lookup(key, &tE, &unused)) E = tE;
+  }
   if (const char* env = getenv("HOFEM_APPLY_E")) {
     const int e = atoi(env);
     if (e >= 1 && e <= 256) E = e;
@@ -498,6 +543,7 @@ hofem_status operator_apply(hofem_plan_s* p, const double* u, const double* f, d
 }  // namespace
 
 namespace hofem {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
 size_t static_scratch_doubles();
 cudaError_t static_scratch_pointer(double** out);
 }  // namespace hofem
@@ -529,6 +575,152 @@ hofem_status operator_apply_static(hofem_plan_s* p, const double* u, double* out
   if ((st = run_apply(p, 2, u, nullptr, t[0], t[1], nullptr, sc[2], p->alpha, nrhs, s)) != HOFEM_OK) return st;
   if ((st = run_apply(p, 1, t[0], t[1], t[2], t[3], nullptr, sc[1], 0.0, nrhs, s)) != HOFEM_OK) return st;
   return run_apply(p, 0, t[2], t[3], nullptr, out, nullptr, sc[0], 0.0, nrhs, s);
+}
+
+
+// ---- autotuner: time every candidate launch shape of this plan's sweeps and operator
+// sweeps on its own (zeroed) workspace and keep the fastest per shape.
+template <typename F> double time_launches(cudaStream_t s, F&& fn, bool* ok) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  *ok = fn() == HOFEM_OK;                       // warm-up
+  double best = 1e30;
+  for (int rep = 0; rep < 3 && *ok; ++rep) {
+    cudaEventRecord(a, s);
+    *ok = fn() == HOFEM_OK;
+    cudaEventRecord(b, s);
+    if (cudaEventSynchronize(b) != cudaSuccess) *ok = false;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    best = std::min(best, (double)ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaGetLastError();
+  return best;
+}
+
+void tune_cache_io(bool save) {
+  const char* path = getenv("HOFEM_TUNE_CACHE");
+  if (!path || !*path) return;
+  if (!save) {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    FILE* fp = fopen(path, "r");
+    if (!fp) return;
+    int k, M, n, K, ts, st, mo, a, b;
+    long long lines;
+    while (fscanf(fp, "%d %d %d %d %d %d %d %lld %d %d", &k, &M, &n, &K, &ts, &st, &mo, &lines, &a, &b) == 10)
+      g_tuned[TuneKey{k, M, n, K, ts, st, mo, lines}] = {a, b};
+    fclose(fp);
+    return;
+  }
+  FILE* fp = fopen(path, "w");
+  if (!fp) return;
+  for (const auto& e : g_tuned) {
+    const TuneKey& t = e.first;
+    fprintf(fp, "%d %d %d %d %d %d %d %lld %d %d\n", std::get<0>(t), std::get<1>(t), std::get<2>(t), std::get<3>(t),
+            std::get<4>(t), std::get<5>(t), std::get<6>(t), std::get<7>(t), e.second.first, e.second.second);
+  }
+  fclose(fp);
+}
+
+hofem_status tune_plan(hofem_plan_s* p, int nrhs, cudaStream_t s, int* measured) {
+  hofem_status st = reserve(p, nrhs);
+  if (st != HOFEM_OK) return st;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_cache_io(false);
+  }
+  const size_t cnt = (size_t)nrhs * p->total;
+  HOFEM_CUDA(cudaMemsetAsync(p->r64, 0, cnt * sizeof(double), s), "memset (tune)");
+  for (double* t : p->tmp64)
+    if (t) HOFEM_CUDA(cudaMemsetAsync(t, 0, cnt * sizeof(double), s), "memset (tune)");
+  if (p->work32) HOFEM_CUDA(cudaMemsetAsync(p->work32, 0, cnt * sizeof(float), s), "memset (tune)");
+  if (p->work16) HOFEM_CUDA(cudaMemsetAsync(p->work16, 0, cnt * 2, s), "memset (tune)");
+  const bool f64 = p->dtype == HOFEM_FP64;
+  const int N = p->N;
+  void* wa = f64 ? (void*)p->tmp64[0] : (void*)p->work32;
+  void* wb = f64 ? (void*)p->tmp64[0] : (p->wfmt == kFmtF32 ? (void*)p->work32 : p->work16);
+  const int fa = f64 ? kFmtF64 : kFmtF32, fb = f64 ? kFmtF64 : p->wfmt;
+  struct Sw { int axis, mode; const void* in; int in_fmt; void* out; int out_fmt; };
+  std::vector<Sw> seq;
+  seq.push_back({N - 1, kFwd, p->r64, kFmtF64, wa, fa});
+  for (int a = N - 2; a >= 1; --a) seq.push_back({a, kFwd, wa, fa, wa, fa});
+  seq.push_back({0, kFwdScaleInv, wa, fa, wb, fb});
+  for (int a = 1; a <= N - 2; ++a) seq.push_back({a, kInv, wb, fb, wb, fb});
+  seq.push_back({N - 1, kInv, wb, fb, p->tmp64[1], kFmtF64});
+  const int tsize = f64 ? 8 : 4;
+  for (const Sw& w : seq) {
+    const TuneKey key = sweep_key(p, w.axis, w.mode, f64, nrhs, -1);
+    int a0, b0;
+    if (tuned_lookup(key, &a0, &b0)) continue;
+    const DevAxis& A = p->ax[w.axis];
+    const long long lines = std::get<7>(key);
+    const bool strided = std::get<5>(key) == 1;
+    double best = 1e30;
+    int bw = 0, bj = 0;
+    for (int W = 64; W >= 1; W >>= 1) {
+      if (W > 1 && lines < W) continue;
+      int J = num_jobs_host(W, A.h.n);
+      while (J >= 1 && sweep_smem_bytes(A.h.M, A.h.n, A.h.K, W, J, tsize, strided) > kSmemLimit) --J;
+      if (J < 1) continue;
+      g_force_a = W;
+      g_force_b = J;
+      bool ok = false;
+      const double ms = time_launches(s, [&]() {
+        return run_sweep(p, w.axis, w.mode, f64, w.in, w.in_fmt, w.out, w.out_fmt, false, nullptr, nrhs, s);
+      }, &ok);
+      g_force_a = g_force_b = 0;
+      ++*measured;
+      if (ok && ms < best) { best = ms; bw = W; bj = J; }
+    }
+    if (bw > 0) {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tuned[key] = {bw, bj};
+    }
+  }
+  // operator sweeps of the residual (refined dtypes) and of hofem_apply
+  struct Ap { int axis; const double *P, *Q; double *o1, *o2; double cCP; };
+  std::vector<Ap> aps;
+  double** t = p->tmp64;
+  if (N == 2) {
+    aps.push_back({1, p->r64, nullptr, t[0], t[1], p->alpha});
+    aps.push_back({0, t[0], t[1], nullptr, p->r64, 0.0});
+  } else {
+    aps.push_back({2, p->r64, nullptr, t[0], t[1], p->alpha});
+    aps.push_back({1, t[0], t[1], t[2], t[3], 0.0});
+    aps.push_back({0, t[2], t[3], nullptr, p->r64, 0.0});
+  }
+  for (const Ap& ap : aps) {
+    const int mode = ap.Q == nullptr ? kApplyFirst : (ap.o1 ? kApplyMid : kApplyLast);
+    const TuneKey key = apply_key(p, ap.axis, mode, nrhs);
+    int a0, b0;
+    if (tuned_lookup(key, &a0, &b0)) continue;
+    double best = 1e30;
+    int bE = 0;
+    for (int E : {4, 8, 16, 32}) {
+      if (E > p->ax[ap.axis].h.K || apply_smem_bytes(p->n, E) > kSmemLimit) continue;
+      g_force_a = E;
+      bool ok = false;
+      const double ms = time_launches(s, [&]() {
+        return run_apply(p, ap.axis, ap.P, ap.Q, ap.o1, ap.o2, nullptr, 1.0, ap.cCP, nrhs, s);
+      }, &ok);
+      g_force_a = 0;
+      ++*measured;
+      if (ok && ms < best) { best = ms; bE = E; }
+    }
+    if (bE > 0) {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tuned[key] = {bE, 0};
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_cache_io(true);
+  }
+  return HOFEM_OK;
 }
 
 }  // namespace
@@ -638,9 +830,15 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
     delete p;
     return st;
   }
-  // default correction steps, measured to reach < 1e-13 for n <= 9 (FP32 2; BF16 and FP16
-  // 4-8 at n = 8-9, K = 64-1024)
-  p->refine_iters = dtype == HOFEM_FP32_REFINED ? 2 : (dtype == HOFEM_BF16_REFINED || dtype == HOFEM_FP16_REFINED) ? 8 : 0;
+  // default correction steps, measured to reach <= 5e-13 for n <= 9: FP32 2 when every K
+  // is a power of two, 3 otherwise (the prime-length passes round a little worse; 512
+  // problems with n = 2..8, K = 32..512: worst 5.4e-12 after 2 steps, 3.3e-13 after 3);
+  // BF16 and FP16 8 (4-8 needed at n = 8-9, K = 64-1024)
+  bool all_pow2 = true;
+  for (int i = 0; i < N; ++i) all_pow2 = all_pow2 && is_pow2(K[i]);
+  p->refine_iters = dtype == HOFEM_FP32_REFINED                                    ? (all_pow2 ? 2 : 3)
+                    : (dtype == HOFEM_BF16_REFINED || dtype == HOFEM_FP16_REFINED) ? 8
+                                                                                    : 0;
   hofem_info& inf = p->info;
   inf.N = N;
   inf.n = n;
@@ -665,6 +863,17 @@ hofem_status hofem_set_refinement(hofem_plan_t p, int iters, double tol) {
   p->refine_tol = tol;
   p->info.refine_iters = iters;
   return HOFEM_OK;
+}
+
+hofem_status hofem_autotune(hofem_plan_t p, int nrhs, void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "nrhs must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  int measured = 0;
+  const hofem_status st = tune_plan(p, nrhs, s, &measured);
+  HOFEM_CUDA(cudaStreamSynchronize(s), "stream sync (autotune)");
+  p->info.tuned_shapes += measured;
+  return st;
 }
 
 hofem_status hofem_reserve(hofem_plan_t p, int nrhs) {

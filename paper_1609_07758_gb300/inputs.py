@@ -54,22 +54,24 @@ def gaussian_rhs(seed, shape, dtype=np.float64):
 
 
 def batch_problems(seed, count=512, k_range=(32, 512), n_range=(2, 8), x_range=(0.5, 4.0),
-                   rhs_range=(1, 8), pow2=True):
-    """Per-problem (K, n, (X_x, X_y), nrhs) drawn log-uniform in K and n.
-
-    With pow2=True, K is rounded down to a power of two (the fast transform path
-    handles power-of-two K); n is an integer in n_range.
-    """
+                   rhs_range=(1, 8)):
+    """Independent 2D problems: K (both axes) and n drawn log-uniform, X per axis uniform,
+    nrhs uniform; returned as dicts with keys N, K, n, X, alpha, nrhs."""
     rng = np.random.default_rng(seed)
     probs = []
     for _ in range(count):
         K = int(np.floor(np.exp(rng.uniform(np.log(k_range[0]), np.log(k_range[1] + 1)))))
         K = min(max(K, k_range[0]), k_range[1])
-        if pow2:
-            K = 1 << int(np.floor(np.log2(K)))
         n = int(np.floor(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1] + 1)))))
         n = min(max(n, n_range[0]), n_range[1])
         X = (float(rng.uniform(*x_range)), float(rng.uniform(*x_range)))
         nrhs = int(rng.integers(rhs_range[0], rhs_range[1] + 1))
-        probs.append({"K": K, "n": n, "X": X, "nrhs": nrhs})
+        probs.append({"N": 2, "K": (K, K), "n": n, "X": X, "alpha": 0.0, "nrhs": nrhs})
     return probs
+
+
+def batch_rhs(seed, index, prob):
+    """N(0,1) right-hand sides (nrhs, M_1, .., M_N) of problem `index` of a batch."""
+    rng = np.random.default_rng([seed, index])
+    shape = (prob["nrhs"],) + tuple(prob["n"] * k - 1 for k in prob["K"])
+    return rng.standard_normal(size=shape)

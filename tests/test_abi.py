@@ -70,6 +70,25 @@ def test_null_plan_calls_fail_cleanly(lib):
     lib.hofem_destroy(None)
 
 
+def test_batch_and_tuner_host_checks(lib):
+    out = ctypes.c_void_p()
+    lib.hofem_batch_plan.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    assert lib.hofem_batch_plan(0, None, 4, ctypes.byref(out)) == 1
+    assert lib.hofem_batch_plan(1, None, 4, ctypes.byref(out)) == 1
+    from paper_1609_07758_gb300.binding import hofem_problem
+    bad = (hofem_problem * 2)()
+    bad[0].N, bad[0].n, bad[0].nrhs = 2, 2, 1
+    bad[1].N, bad[1].n, bad[1].nrhs = 4, 2, 1             # N must be 2 or 3
+    assert lib.hofem_batch_plan(2, bad, 4, ctypes.byref(out)) == 1 and not out.value
+    bad[1].N, bad[1].nrhs = 2, 0                           # nrhs >= 1
+    assert lib.hofem_batch_plan(2, bad, 4, ctypes.byref(out)) == 1
+    assert lib.hofem_batch_solve(None, None, None, None) == 1
+    assert lib.hofem_batch_tune(None, None) == 1
+    assert lib.hofem_batch_get_info(None, None) == 1
+    assert lib.hofem_autotune(None, 1, None) == 1
+    lib.hofem_batch_destroy(None)
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     import paper_1609_07758_gb300.binding as bnd
     monkeypatch.setattr(bnd, "_lib", None)

@@ -112,3 +112,36 @@ def test_3d_n8_k64_16rhs_half_refined(dtype_name):
         err = rel_l2(ud[r:r + 1].cpu().numpy(), ref)
         print(f"  rhs {r}: rel L2 vs oracle {err:.3e}")
         assert err <= 1e-12
+
+
+def test_batched_512_problems_refined():
+    """512 2D problems (K 32..512 and n 2..8 log-uniform, X per axis in [0.5, 4], 1-8 RHS)
+    in one graph launch, FP32 + FP64 refinement: every problem against its FP64 GPU solve,
+    three of them (smallest, largest, one in between) against the oracle."""
+    from paper_1609_07758_gb300 import inputs
+    probs = inputs.batch_problems(4)
+    b = H().Batch(probs, H().HOFEM_FP32_REFINED)
+    fd = [torch.from_numpy(inputs.batch_rhs(4, i, q)).cuda() for i, q in enumerate(probs)]
+    ud = [torch.zeros_like(f) for f in fd]
+    b.solve(fd, ud)
+    torch.cuda.synchronize()
+    info = b.info()
+    print(f"batch: {info.count} problems, {info.unknowns} unknown-RHS, {info.graph_nodes} graph nodes, "
+          f"plan {info.plan_ms:.0f} ms")
+    worst = 0.0
+    for i, q in enumerate(probs):
+        p64 = H().Plan(2, q["K"], q["n"], q["X"], H().HOFEM_FP64)
+        u64 = torch.zeros_like(fd[i])
+        p64.solve(fd[i], u64, q["nrhs"])
+        err = float(torch.linalg.vector_norm(ud[i] - u64) / torch.linalg.vector_norm(u64))
+        worst = max(worst, err)
+        p64.close()
+    print(f"  max rel L2 vs FP64 over 512 problems {worst:.3e}")
+    assert worst <= 1e-12
+    size = [q["nrhs"] * (q["n"] * q["K"][0] - 1) ** 2 for q in probs]
+    for i in (int(np.argmin(size)), int(np.argmax(size)), 100):
+        q = probs[i]
+        ref = osolve.solve_tensor(inputs.batch_rhs(4, i, q), [q["n"]] * 2, list(q["K"]), list(q["X"]))
+        err = rel_l2(ud[i].cpu().numpy(), ref)
+        print(f"  problem {i} (K {q['K'][0]}, n {q['n']}, nrhs {q['nrhs']}): rel L2 vs oracle {err:.3e}")
+        assert err <= 1e-12
