@@ -339,7 +339,7 @@ TuneKey apply_key(const hofem_plan_s* p, int axis, int mode, long long nrhs) {
 hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void* in, int in_fmt, void* out,
                        int out_fmt, bool accumulate, double* norms, long long nrhs, cudaStream_t s,
                        long long lines_override = -1, const unsigned long long* in_amax = nullptr,
-                       const unsigned long long* out_amax = nullptr) {
+                       const unsigned long long* out_amax = nullptr, int norm_slot = 0) {
   const DevAxis& A = p->ax[axis];
   SweepParams P{};
   Geo g = geometry(p, axis);
@@ -383,6 +383,7 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   P.lamR = (P.lscale && mode == kInv && axis < p->N - 1) ? (const void*)p->ax[axis + 1].lam32 : nullptr;
   P.accumulate = accumulate;
   P.norms = norms;
+  P.norm_slot = norm_slot;
   P.mix = f64 ? (const void*)A.mix64 : (const void*)A.mix32;
   P.mixNP = A.mixNP;
   P.evec = f64 ? (const void*)A.evec64 : (const void*)A.evec32;
@@ -439,7 +440,7 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
 // number; after the division rounding errors stay relative.  FP16 adds an exact
 // power-of-two scale of each right-hand side.
 hofem_status solve_once(hofem_plan_s* p, const double* f, double* u, int nrhs, bool f64, bool accumulate,
-                        double* norms, cudaStream_t s) {
+                        double* norms, int norm_slot, cudaStream_t s) {
   hofem_status st;
   void* wa = f64 ? (void*)u : (void*)p->work32;                                   // before the division
   void* wb = f64 ? (void*)u : (p->wfmt == kFmtF32 ? (void*)p->work32 : p->work16);  // after it
@@ -460,7 +461,7 @@ hofem_status solve_once(hofem_plan_s* p, const double* f, double* u, int nrhs, b
   if ((st = run_sweep(p, 0, kFwdScaleInv, f64, wa, fa, wb, fb, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
   for (int a = 1; a <= N - 2; ++a)
     if ((st = run_sweep(p, a, kInv, f64, wb, fb, wb, fb, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
-  return run_sweep(p, N - 1, kInv, f64, wb, fb, u, kFmtF64, accumulate, norms, nrhs, s, -1, nullptr, amax);
+  return run_sweep(p, N - 1, kInv, f64, wb, fb, u, kFmtF64, accumulate, norms, nrhs, s, -1, nullptr, amax, norm_slot);
 }
 
 // One operator sweep along `axis` (modes in residual.cuh): Q == nullptr is the first
@@ -892,20 +893,22 @@ hofem_status hofem_solve(hofem_plan_t p, const double* f, double* u, int nrhs, v
     return fail(HOFEM_ERR_INVALID_ARG, "f and u must differ for refined solves");
   hofem_status st;
   if (p->dtype == HOFEM_FP64) {
-    st = solve_once(p, f, u, nrhs, true, false, nullptr, s);
+    st = solve_once(p, f, u, nrhs, true, false, nullptr, 0, s);
     p->info.iterations = 0;
     p->info.converged = 1;
     return st;
   }
   if ((st = reserve(p, nrhs)) != HOFEM_OK) return st;
-  if ((st = solve_once(p, f, u, nrhs, false, false, nullptr, s)) != HOFEM_OK) return st;
   const int iters = refined ? p->refine_iters : 0;
+  // norms[2 r + 1] = ||u||^2 of the first solve, norms[2 r] = ||delta||^2 of the last step
+  if (iters > 0) HOFEM_CUDA(cudaMemsetAsync(p->norms, 0, 2 * (size_t)nrhs * sizeof(double), s), "memset norms");
+  if ((st = solve_once(p, f, u, nrhs, false, false, iters > 0 ? p->norms : nullptr, 1, s)) != HOFEM_OK) return st;
   int done = 0;
   bool converged = false;
   for (int i = 0; i < iters; ++i) {
     if ((st = operator_apply(p, u, f, p->r64, nrhs, s)) != HOFEM_OK) return st;
-    HOFEM_CUDA(cudaMemsetAsync(p->norms, 0, 2 * (size_t)nrhs * sizeof(double), s), "memset norms");
-    if ((st = solve_once(p, p->r64, u, nrhs, false, true, p->norms, s)) != HOFEM_OK) return st;
+    HOFEM_CUDA(cudaMemset2DAsync(p->norms, 2 * sizeof(double), 0, sizeof(double), nrhs, s), "memset norms");
+    if ((st = solve_once(p, p->r64, u, nrhs, false, true, p->norms, 0, s)) != HOFEM_OK) return st;
     ++done;
     if (p->refine_tol > 0.0) {
       HOFEM_CUDA(cudaMemcpyAsync(p->h_norms, p->norms, 2 * (size_t)nrhs * sizeof(double), cudaMemcpyDeviceToHost, s),

@@ -560,7 +560,7 @@ __device__ __forceinline__ void mix_dispatch(const Tile<T> tl, int W, int n, int
   }
 }
 
-template <typename T>
+template <typename T, bool GK>
 __device__ void forward_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf, T* tsave, int W, int n,
                                   int K, const SweepParams& P, const T* __restrict__ mix,
                                   const T* __restrict__ evec, const typename Cx<T>::type* __restrict__ tw) {
@@ -584,7 +584,7 @@ __device__ void forward_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
   const int nj_tot = num_jobs(W, n), J = P.jobs_per_batch;
   for (int j0 = 0; j0 < nj_tot; j0 += J) {
     const int nj = min(J, nj_tot - j0);
-    if (P.pow2) {
+    if constexpr (!GK) {
       dst_load<T>(tl, fbuf, j0, nj, W, n, K, false, tw);
       __syncthreads();
       fft_all<T>(fbuf, logK, 2 * nj, P, tw);
@@ -628,7 +628,7 @@ __device__ void forward_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
   __syncthreads();
 }
 
-template <typename T>
+template <typename T, bool GK>
 __device__ void inverse_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf, T* gsave, int W, int n,
                                   int K, const SweepParams& P, const T* __restrict__ mix,
                                   const T* __restrict__ evec, const typename Cx<T>::type* __restrict__ tw) {
@@ -642,7 +642,7 @@ __device__ void inverse_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
   for (int j0 = 0; j0 < nj_tot; j0 += J) {
     const int nj = min(J, nj_tot - j0);
     const typename Cx<T>::type* res = fbuf;
-    if (P.pow2) {
+    if constexpr (!GK) {
       dst_load<T>(tl, fbuf, j0, nj, W, n, K, true, tw);
       __syncthreads();
       fft_all<T>(fbuf, logK, 2 * nj, P, tw);
@@ -655,7 +655,7 @@ __device__ void inverse_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
     const int items = nj * K;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       int jb, j;
-      if (P.pow2) {
+      if constexpr (!GK) {
         jb = it >> logK;
         j = (it & (K - 1)) + 1;                        // j = 1..K
       } else {
@@ -664,7 +664,7 @@ __device__ void inverse_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
       }
       const Job job = job_of(j0 + jb, W, logW, n);
       T a0 = (T)0, b0 = (T)0, a1 = (T)0, b1 = (T)0;   // D at j-1 and at j
-      if (P.pow2) {
+      if constexpr (!GK) {
         if (j - 1 >= 1) dst_out<T>(res, jb, K, logK, j - 1, &a0, &b0, P);
         if (j <= K - 1) dst_out<T>(res, jb, K, logK, j, &a1, &b1, P);
       } else {
@@ -906,13 +906,22 @@ __device__ void wfft_dispatch(const Tile<float>& tl, float2* X, int XS, float2* 
   }
 }
 
-// load element i of an array in format fmt, times the power of two sc
-template <typename T> __device__ __forceinline__ T ldcvt(const void* p, size_t i, int fmt, double sc) {
+// load element i of an array in format fmt, times the power of two sc (applied before
+// any narrowing: FP64 inputs far outside FP32's range keep their bits)
+template <typename T> __device__ __forceinline__ T ldcvt_scaled(const void* p, size_t i, int fmt, double sc) {
+  if (fmt == kFmtF64) return (T)(__ldg((const double*)p + i) * sc);
+  if (fmt == kFmtBF16) return (T)__bfloat162float(__ldg((const __nv_bfloat16*)p + i)) * (T)sc;
+  if (fmt == kFmtF16) return (T)__half2float(__ldg((const __half*)p + i)) * (T)sc;
+  return (T)__ldg((const float*)p + i) * (T)sc;
+}
+
+// load element i of an array in format fmt
+template <typename T> __device__ __forceinline__ T ldcvt(const void* p, size_t i, int fmt) {
   switch (fmt) {
-    case kFmtF64: return (T)(__ldg((const double*)p + i) * sc);
-    case kFmtBF16: return (T)__bfloat162float(__ldg((const __nv_bfloat16*)p + i)) * (T)sc;
-    case kFmtF16: return (T)__half2float(__ldg((const __half*)p + i)) * (T)sc;
-    default: return (T)__ldg((const float*)p + i) * (T)sc;
+    case kFmtF64: return (T)__ldg((const double*)p + i);
+    case kFmtBF16: return (T)__bfloat162float(__ldg((const __nv_bfloat16*)p + i));
+    case kFmtF16: return (T)__half2float(__ldg((const __half*)p + i));
+    default: return (T)__ldg((const float*)p + i);
   }
 }
 
@@ -923,7 +932,9 @@ __device__ __forceinline__ double amax_scale(const unsigned long long* amax, lon
   return m > 0.0 ? ldexp(1.0, e - ilogb(m) - 1) : 1.0;
 }
 
-template <typename T, bool WF>
+// GK: K is not a power of two (mixed-radix DST passes); a separate instantiation keeps
+// the power-of-two kernel free of the general path.
+template <typename T, bool WF, bool GK>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) sweep_kernel(const SweepParams P) {
   using C = typename Cx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -969,7 +980,9 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
       const int e = e0 + u * blockDim.x;
-      v[u] = (e < total && valid(e)) ? ldcvt<T>(P.in, (size_t)gaddr(e), P.in_fmt, in_sc) : (T)0;
+      v[u] = (e < total && valid(e))
+                 ? (P.in_amax ? ldcvt_scaled<T>(P.in, (size_t)gaddr(e), P.in_fmt, in_sc) : ldcvt<T>(P.in, (size_t)gaddr(e), P.in_fmt))
+                 : (T)0;
     }
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
@@ -1016,7 +1029,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
       wfft_dispatch<true>(tl, fbuf, P.wf_xs, fbuf + (size_t)num_jobs(W, n) * P.wf_xs, save, W, n, K, P, mix, evec,
                           tw, 2 * P.fbuf_complex);
   } else {
-    if (P.mode & kFwd) forward_transform<T>(tl, fbuf, save, W, n, K, P, mix, evec, tw);
+    if (P.mode & kFwd) forward_transform<T, GK>(tl, fbuf, save, W, n, K, P, mix, evec, tw);
   }
   if (P.mode == kFwdScaleInv) {
     const T* lam = (const T*)P.lam;
@@ -1031,7 +1044,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
       wfft_dispatch<false>(tl, fbuf, P.wf_xs, fbuf + (size_t)num_jobs(W, n) * P.wf_xs, save, W, n, K, P, mix, evec,
                            tw, 2 * P.fbuf_complex);
   } else {
-    if (P.mode & kInv) inverse_transform<T>(tl, fbuf, save, W, n, K, P, mix, evec, tw);
+    if (P.mode & kInv) inverse_transform<T, GK>(tl, fbuf, save, W, n, K, P, mix, evec, tw);
   }
 
   if (P.lscale && P.out_fmt != kFmtF64) {
@@ -1043,26 +1056,29 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
     }
     __syncthreads();
   }
-  // ---- store (same element order as the load)
-  double s_d = 0.0, s_u = 0.0;
+  // ---- store (same element order as the load); optional sum of squares of the result
+  T s_d = (T)0;
+  const bool want_norm = P.norms != nullptr, scaled_out = P.out_amax != nullptr;
   for (int e0 = threadIdx.x; e0 < total; e0 += UNR * blockDim.x) {
     if (P.out_fmt == kFmtF64) {
       double* out = (double*)P.out;
       double prev[UNR];
+      if (P.accumulate) {
 #pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        const int e = e0 + u * blockDim.x;
-        prev[u] = (P.accumulate && e < total && valid(e)) ? out[gaddr(e)] : 0.0;
+        for (int u = 0; u < UNR; ++u) {
+          const int e = e0 + u * blockDim.x;
+          prev[u] = (e < total && valid(e)) ? out[gaddr(e)] : 0.0;
+        }
       }
 #pragma unroll
       for (int u = 0; u < UNR; ++u) {
         const int e = e0 + u * blockDim.x;
         if (e < total && valid(e)) {
-          const double v = (double)tile[e + (e >> TileSwz<T>::v)] * out_sc;
-          const double r = prev[u] + v;
-          out[gaddr(e)] = r;
-          s_d += v * v;
-          s_u += r * r;
+          const T tv = tile[e + (e >> TileSwz<T>::v)];
+          double v = (double)tv;
+          if (scaled_out) v *= out_sc;
+          out[gaddr(e)] = P.accumulate ? prev[u] + v : v;
+          if (want_norm) s_d += tv * tv;
         }
       }
     } else {
@@ -1078,26 +1094,17 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
       }
     }
   }
-  if (P.norms) {
+  if (want_norm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double sd = (double)s_d * out_sc * out_sc;
 #pragma unroll
-    for (int o2 = 16; o2 > 0; o2 >>= 1) {
-      s_d += __shfl_xor_sync(0xffffffffu, s_d, o2);
-      s_u += __shfl_xor_sync(0xffffffffu, s_u, o2);
-    }
-    if (lane == 0) {
-      red[2 * warp] = s_d;
-      red[2 * warp + 1] = s_u;
-    }
+    for (int o2 = 16; o2 > 0; o2 >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o2);
+    if (lane == 0) red[warp] = sd;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double a = 0.0, c = 0.0;
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-        a += red[2 * i];
-        c += red[2 * i + 1];
-      }
-      atomicAdd(&P.norms[2 * rhs], a);
-      atomicAdd(&P.norms[2 * rhs + 1], c);
+      double a = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += red[i];
+      atomicAdd(&P.norms[2 * rhs + P.norm_slot], a);
     }
   }
 }
@@ -1167,21 +1174,25 @@ int sweep_max_jobs(int K, int tsize, int threads) {
 }
 
 cudaError_t sweep_set_smem_limits() {
-  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(sweep_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(sweep_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<float, false, false>, a, 232448);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep_kernel<float, true, false>, a, 232448);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep_kernel<float, false, true>, a, 232448);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep_kernel<double, false, false>, a, 232448);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep_kernel<double, false, true>, a, 232448);
+  return e;
 }
 
 cudaError_t launch_sweep_f32(const SweepParams& p, cudaStream_t s) {
-  if (p.wfft) sweep_kernel<float, true><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
-  else sweep_kernel<float, false><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
+  if (p.wfft) sweep_kernel<float, true, false><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
+  else if (p.pow2) sweep_kernel<float, false, false><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
+  else sweep_kernel<float, false, true><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sweep_f64(const SweepParams& p, cudaStream_t s) {
-  sweep_kernel<double, false><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
+  if (p.pow2) sweep_kernel<double, false, false><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
+  else sweep_kernel<double, false, true><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
   return cudaGetLastError();
 }
 

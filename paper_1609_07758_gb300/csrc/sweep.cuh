@@ -48,7 +48,8 @@ struct SweepParams {
   // by column (null: 0)
   int lscale;
   const void* lamR;
-  double* norms;              // if non-null: per rhs {sum result^2, sum out_new^2} (atomics)
+  double* norms;              // if non-null: norms[2 rhs + norm_slot] += sum result^2 (atomics)
+  int norm_slot;
   // axis tables, in the work precision T
   const void* mix;            // (K-1) n NP, rows padded to NP entries
   int mixNP;
