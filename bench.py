@@ -45,6 +45,7 @@ def parse_args():
     ap.add_argument("--refine-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the plan-time autotuner (built-in launch shapes)")
     ap.add_argument("--elements", type=int, default=K_ELEM,
                     help="elements per axis (default 1024, the benchmark workload; smaller K for profiling)")
     args = ap.parse_args()
@@ -246,6 +247,10 @@ def main():
     plan.set_refinement(args.refine_iters)
     plan.reserve(1)
     plan64 = hofem.Plan(2, K2, N_ORDER, X2, hofem.HOFEM_FP64)
+    if not args.no_tune:
+        # plan-time launch-shape measurement (outside every timed region)
+        plan.autotune(1)
+        plan64.autotune(1)
 
     # accuracy of the mixed solve against the plain FP64 GPU solve (oracle parity is in tests/)
     plan64.solve(f, u64, 1, stream)
@@ -331,7 +336,8 @@ def main():
         "vs_baseline": value / PAPER_UNKNOWNS_PER_S, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": 2, "n": N_ORDER, "K": [K_ELEM, K_ELEM], "unknowns": UNKNOWNS,
                    "nrhs": 1, "path": "FP32 sweeps + FP64 residual refinement",
-                   "refine_iters": args.refine_iters, "l2": "inputs larger than L2 (680 MB FP64 arrays)",
+                   "refine_iters": args.refine_iters, "launch_shapes": "built-in" if args.no_tune else "autotuned at plan time",
+                   "l2": "inputs larger than L2 (680 MB FP64 arrays)",
                    "parallelism": f"{world} independent problems (one per GPU)"},
         "fp64_plain": {"value": world * UNKNOWNS / (ms_fp64 / 1e3), "ms_per_step": ms_fp64},
         "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed,

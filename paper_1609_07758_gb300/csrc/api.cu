@@ -587,7 +587,7 @@ template <typename F> double time_launches(cudaStream_t s, F&& fn, bool* ok) {
   cudaEventCreate(&b);
   *ok = fn() == HOFEM_OK;                       // warm-up
   double best = 1e30;
-  for (int rep = 0; rep < 3 && *ok; ++rep) {
+  for (int rep = 0; rep < 5 && *ok; ++rep) {
     cudaEventRecord(a, s);
     *ok = fn() == HOFEM_OK;
     cudaEventRecord(b, s);
@@ -645,13 +645,14 @@ hofem_status tune_plan(hofem_plan_s* p, int nrhs, cudaStream_t s, int* measured)
   void* wa = f64 ? (void*)p->tmp64[0] : (void*)p->work32;
   void* wb = f64 ? (void*)p->tmp64[0] : (p->wfmt == kFmtF32 ? (void*)p->work32 : p->work16);
   const int fa = f64 ? kFmtF64 : kFmtF32, fb = f64 ? kFmtF64 : p->wfmt;
-  struct Sw { int axis, mode; const void* in; int in_fmt; void* out; int out_fmt; };
+  // the last inverse sweep is timed as the correction solves run it (accumulating, with norms)
+  struct Sw { int axis, mode; const void* in; int in_fmt; void* out; int out_fmt; bool acc; };
   std::vector<Sw> seq;
-  seq.push_back({N - 1, kFwd, p->r64, kFmtF64, wa, fa});
-  for (int a = N - 2; a >= 1; --a) seq.push_back({a, kFwd, wa, fa, wa, fa});
-  seq.push_back({0, kFwdScaleInv, wa, fa, wb, fb});
-  for (int a = 1; a <= N - 2; ++a) seq.push_back({a, kInv, wb, fb, wb, fb});
-  seq.push_back({N - 1, kInv, wb, fb, p->tmp64[1], kFmtF64});
+  seq.push_back({N - 1, kFwd, p->r64, kFmtF64, wa, fa, false});
+  for (int a = N - 2; a >= 1; --a) seq.push_back({a, kFwd, wa, fa, wa, fa, false});
+  seq.push_back({0, kFwdScaleInv, wa, fa, wb, fb, false});
+  for (int a = 1; a <= N - 2; ++a) seq.push_back({a, kInv, wb, fb, wb, fb, false});
+  seq.push_back({N - 1, kInv, wb, fb, p->tmp64[1], kFmtF64, !f64});
   const int tsize = f64 ? 8 : 4;
   for (const Sw& w : seq) {
     const TuneKey key = sweep_key(p, w.axis, w.mode, f64, nrhs, -1);
@@ -671,7 +672,8 @@ hofem_status tune_plan(hofem_plan_s* p, int nrhs, cudaStream_t s, int* measured)
       g_force_b = J;
       bool ok = false;
       const double ms = time_launches(s, [&]() {
-        return run_sweep(p, w.axis, w.mode, f64, w.in, w.in_fmt, w.out, w.out_fmt, false, nullptr, nrhs, s);
+        return run_sweep(p, w.axis, w.mode, f64, w.in, w.in_fmt, w.out, w.out_fmt, w.acc, w.acc ? p->norms : nullptr,
+                         nrhs, s);
       }, &ok);
       g_force_a = g_force_b = 0;
       ++*measured;
