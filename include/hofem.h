@@ -133,6 +133,20 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
  * which synchronises the stream once per step.  tol = 0 keeps a fixed count (capturable). */
 hofem_status hofem_set_refinement(hofem_plan_t plan, int iters, double tol);
 
+/* The (n+1)-point Gauss-Legendre quadrature points of the load vector along `axis`
+ * (Sect. 2 par. 5): x[e (n+1) + g] = e h + (1 + xi_g) h / 2 for the elements e = 0..K-1,
+ * xi_g ascending on [-1, 1], h = X / K.  x: HOST array of K (n+1) doubles.  Synchronous. */
+hofem_status hofem_quadrature_points(hofem_plan_t plan, int axis, double* x);
+
+/* The FEM average f^h of Sect. 2 par. 4, f^h_p = prod_i (2/h_i) int f phi_p, by the
+ * (n+1)-point Gauss-Legendre rule on every element along every axis (Sect. 2 par. 5),
+ * from samples of f at the tensor product of the quadrature points:
+ * fq: device FP64 (nrhs, K_1(n+1), .., K_N(n+1)), C-order, axis i indexed e (n+1) + g as in
+ * hofem_quadrature_points; fh: device FP64 (nrhs, M_1..M_N), ready for hofem_solve.
+ * Two plan-owned intermediate arrays are allocated on first use (or when nrhs grows).
+ * Asynchronous on stream; fq != fh. */
+hofem_status hofem_load(hofem_plan_t plan, const double* fq, double* fh, int nrhs, void* stream);
+
 /* Autotuner: time every candidate launch shape (sweep lines per CTA W and DST batch J;
  * operator elements per CTA E) of this plan's solve and apply for nrhs right-hand sides
  * on its own workspace, and keep the fastest per shape in a process-wide table that

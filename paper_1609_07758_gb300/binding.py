@@ -23,7 +23,8 @@ EXPORTED = (
     "hofem_residual", "hofem_transform1d", "hofem_get_eigen", "hofem_get_info",
     "hofem_destroy", "hofem_status_string", "hofem_last_error", "hofem_profile", "hofem_get_profile",
     "hofem_apply_static", "hofem_autotune", "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve",
-    "hofem_batch_get_info", "hofem_batch_get_plan", "hofem_batch_destroy",
+    "hofem_batch_get_info", "hofem_batch_get_plan", "hofem_batch_destroy", "hofem_quadrature_points",
+    "hofem_load",
 )
 
 
@@ -95,6 +96,8 @@ def load_library():
     lib.hofem_last_error.argtypes = []
     lib.hofem_last_error.restype = ctypes.c_char_p
     lib.hofem_autotune.argtypes = [P, I, V]
+    lib.hofem_quadrature_points.argtypes = [P, I, ctypes.POINTER(D)]
+    lib.hofem_load.argtypes = [P, V, V, I, V]
     lib.hofem_batch_plan.argtypes = [I, ctypes.POINTER(hofem_problem), I, ctypes.POINTER(P)]
     lib.hofem_batch_tune.argtypes = [P, V]
     lib.hofem_batch_solve.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), V]
@@ -106,7 +109,7 @@ def load_library():
                  "hofem_residual", "hofem_transform1d", "hofem_get_eigen", "hofem_get_info",
                  "hofem_profile", "hofem_get_profile", "hofem_apply_static", "hofem_autotune",
                  "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve", "hofem_batch_get_info",
-                 "hofem_batch_get_plan"):
+                 "hofem_batch_get_plan", "hofem_quadrature_points", "hofem_load"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -266,6 +269,19 @@ class Plan:
 
     def autotune(self, nrhs, stream=None):
         hofem_autotune(self.handle, nrhs, stream)
+
+    def quadrature_points(self, axis):
+        """The K (n+1) Gauss-Legendre points of the load vector along `axis` (numpy)."""
+        import numpy as np
+        x = np.zeros(self.K[axis] * (self.n + 1))
+        _check(load_library().hofem_quadrature_points(self.handle, int(axis),
+                                                      x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "hofem_quadrature_points")
+        return x
+
+    def load(self, fq, fh, nrhs, stream=None):
+        """fh = f^h from samples fq of f at the tensor product of the quadrature points."""
+        _check(load_library().hofem_load(self.handle, _ptr(fq), _ptr(fh), int(nrhs), _stream(stream)), "hofem_load")
 
     def profile(self, enable):
         hofem_profile(self.handle, enable)

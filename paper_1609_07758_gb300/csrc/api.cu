@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "load.cuh"
 #include "residual.cuh"
 #include "sweep.cuh"
 
@@ -69,6 +70,10 @@ struct hofem_plan_s {
   bool refined = false;          // *_REFINED dtype
   unsigned long long* amax = nullptr;   // per-rhs max |rhs| (FP16 work arrays only)
   int amax_exp = 10;             // FP16: scaled right-hand sides have |max| in [2^(e-1), 2^e)
+  // load-vector quadrature (hofem_load): tables and the two intermediate axis buffers
+  std::vector<double> load_T, load_xi;
+  double* ld[2] = {nullptr, nullptr};
+  size_t ld_count = 0;
   double* r64 = nullptr;         // residual
   double* tmp64[4] = {nullptr, nullptr, nullptr, nullptr};
   double* norms = nullptr;       // 2 per rhs
@@ -842,6 +847,7 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
   p->refine_iters = dtype == HOFEM_FP32_REFINED                                    ? (all_pow2 ? 2 : 3)
                     : (dtype == HOFEM_BF16_REFINED || dtype == HOFEM_FP16_REFINED) ? 8
                                                                                     : 0;
+  element_load_table(n, &p->load_T, &p->load_xi);
   hofem_info& inf = p->info;
   inf.N = N;
   inf.n = n;
@@ -865,6 +871,67 @@ hofem_status hofem_set_refinement(hofem_plan_t p, int iters, double tol) {
   p->refine_iters = iters;
   p->refine_tol = tol;
   p->info.refine_iters = iters;
+  return HOFEM_OK;
+}
+
+hofem_status hofem_quadrature_points(hofem_plan_t p, int axis, double* x) {
+  if (!p || !x) return fail(HOFEM_ERR_INVALID_ARG, "plan or x is NULL");
+  if (axis < 0 || axis >= p->N) return fail(HOFEM_ERR_INVALID_ARG, "axis out of range");
+  const int G = p->n + 1, K = p->K[axis];
+  const double h = p->X[axis] / K;
+  for (int e = 0; e < K; ++e)
+    for (int g = 0; g < G; ++g) x[(size_t)e * G + g] = e * h + (p->load_xi[g] + 1.0) * h / 2.0;
+  return HOFEM_OK;
+}
+
+hofem_status hofem_load(hofem_plan_t p, const double* fq, double* fh, int nrhs, void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (!fq || !fh || nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or nrhs");
+  if ((const void*)fq == (const void*)fh) return fail(HOFEM_ERR_INVALID_ARG, "fq and fh must differ");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = p->N, n = p->n, G = n + 1;
+  long long L[3];                                   // current length of every axis
+  for (int i = 0; i < N; ++i) L[i] = (long long)p->K[i] * G;
+  // intermediates after axes N-1 .. 1 (axis 0 writes fh)
+  size_t need = 0;
+  {
+    long long Lt[3] = {L[0], L[1], L[2]};
+    for (int a = N - 1; a >= 1; --a) {
+      Lt[a] = p->M[a];
+      size_t cnt = (size_t)nrhs;
+      for (int i = 0; i < N; ++i) cnt *= (size_t)Lt[i];
+      need = std::max(need, cnt);
+    }
+  }
+  if (need > p->ld_count) {
+    cudaFree(p->ld[0]);
+    cudaFree(p->ld[1]);
+    p->ld[0] = p->ld[1] = nullptr;
+    p->ld_count = 0;
+    HOFEM_CUDA(cudaMalloc(&p->ld[0], need * sizeof(double)), "cudaMalloc(load buffer)");
+    HOFEM_CUDA(cudaMalloc(&p->ld[1], need * sizeof(double)), "cudaMalloc(load buffer)");
+    p->ld_count = need;
+  }
+  LoadParams P{};
+  P.n = n;
+  for (int i = 0; i < G * G; ++i) P.T[i] = p->load_T[i];
+  const double* in = fq;
+  int buf = 0;
+  for (int a = N - 1; a >= 0; --a) {
+    P.in = in;
+    P.out = a == 0 ? fh : p->ld[buf];
+    P.K = p->K[a];
+    P.M = p->M[a];
+    P.outer = nrhs;
+    for (int i = 0; i < a; ++i) P.outer *= L[i];
+    P.inner = 1;
+    for (int i = a + 1; i < N; ++i) P.inner *= p->M[i];
+    HOFEM_CUDA(launch_load(P, s), "load launch");
+    p->info.kernel_launches += 1;
+    L[a] = p->M[a];
+    in = P.out;
+    buf ^= 1;
+  }
   return HOFEM_OK;
 }
 
@@ -1028,6 +1095,8 @@ void hofem_destroy(hofem_plan_t p) {
   for (auto e : p->pool) cudaEventDestroy(e);
   p->pool.clear();
   free_workspace(p);
+  cudaFree(p->ld[0]);
+  cudaFree(p->ld[1]);
   for (int i = 0; i < p->N; ++i) free_axis(p->ax[i]);
   delete p;
 }

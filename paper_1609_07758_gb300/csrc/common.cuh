@@ -39,4 +39,7 @@ struct AxisTables {
 
 hofem_status build_axis_tables(int n, int K, double X, AxisTables* out, std::string* err);
 
+// (n+1)-point Gauss-Legendre nodes xi (ascending) and T[a (n+1) + g] = w_g e_a(xi_g).
+void element_load_table(int n, std::vector<double>* T, std::vector<double>* xi);
+
 }  // namespace hofem

@@ -1,0 +1,71 @@
+// FEM average f^h of the right-hand side (Sect. 2 par. 4), by the (n+1)-point
+// Gauss-Legendre rule on every element along every axis (Sect. 2 par. 5).  On an element
+// the map x = x_{e} + (xi + 1) h / 2 turns (2/h) int f e_a into sum_g w_g e_a(xi_g) f(x_g),
+// so one axis maps K (n+1) samples per line to M = nK - 1 entries:
+//   interior a = 1..n-1 of element e:  sum_g T[a][g] q_{e,g}
+//   node between elements e and e+1:   sum_g T[n][g] q_{e,g} + sum_g T[0][g] q_{e+1,g}
+// (the outer nodes are Dirichlet and dropped).  The tensor product is applied one axis at
+// a time; one thread per (line, element) writes that element's n owned entries.
+#include <algorithm>
+
+#include "common.cuh"
+#include "load.cuh"
+
+namespace hofem {
+
+namespace {
+
+template <int N>
+__global__ void __launch_bounds__(256) load_axis_kernel(const __grid_constant__ LoadParams P) {
+  constexpr int G = N + 1;
+  const long long inner = P.inner, K = P.K, total = P.outer * K * inner;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long c = idx % inner, rest = idx / inner;
+    const long long e = rest % K, o = rest / K;
+    const double* q = P.in + (o * K * G + e * G) * inner + c;
+    double* out = P.out + (o * P.M) * inner + c;
+    double v[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) v[g] = __ldg(q + (long long)g * inner);
+#pragma unroll
+    for (int a = 1; a < N; ++a) {
+      double s = 0.0;
+#pragma unroll
+      for (int g = 0; g < G; ++g) s = fma(P.T[a * G + g], v[g], s);
+      out[(e * N + a - 1) * inner] = s;
+    }
+    if (e + 1 < K) {
+      double s = 0.0;
+#pragma unroll
+      for (int g = 0; g < G; ++g) s = fma(P.T[N * G + g], v[g], s);
+      const double* qn = q + (long long)G * inner;
+#pragma unroll
+      for (int g = 0; g < G; ++g) s = fma(P.T[g], __ldg(qn + (long long)g * inner), s);
+      out[((e + 1) * N - 1) * inner] = s;
+    }
+  }
+}
+
+template <int N> cudaError_t launch_n(const LoadParams& p, cudaStream_t s) {
+  const long long total = p.outer * p.K * p.inner;
+  const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 16);
+  load_axis_kernel<N><<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_load(const LoadParams& p, cudaStream_t s) {
+  switch (p.n) {
+#define HOFEM_LD_CASE(NN) \
+  case NN: return launch_n<NN>(p, s);
+    HOFEM_LD_CASE(1) HOFEM_LD_CASE(2) HOFEM_LD_CASE(3) HOFEM_LD_CASE(4) HOFEM_LD_CASE(5) HOFEM_LD_CASE(6)
+    HOFEM_LD_CASE(7) HOFEM_LD_CASE(8) HOFEM_LD_CASE(9) HOFEM_LD_CASE(10) HOFEM_LD_CASE(11) HOFEM_LD_CASE(12)
+    HOFEM_LD_CASE(13) HOFEM_LD_CASE(14) HOFEM_LD_CASE(15) HOFEM_LD_CASE(16)
+#undef HOFEM_LD_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace hofem

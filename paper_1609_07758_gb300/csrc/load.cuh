@@ -1,0 +1,19 @@
+// Launch parameters of the load-vector quadrature pass (load.cu).
+#pragma once
+#include "common.cuh"
+
+namespace hofem {
+
+constexpr int kLoadTab = (kMaxN + 1) * (kMaxN + 1);
+
+struct LoadParams {
+  const double* in;           // (outer, K (n+1), inner): samples at the quadrature points
+  double* out;                // (outer, M, inner): load-vector entries along this axis
+  long long outer, inner;
+  int K, n, M;
+  double T[kLoadTab];         // T[a (n+1) + g] = w_g e_a(xi_g), as kernel parameters
+};
+
+cudaError_t launch_load(const LoadParams& p, cudaStream_t s);
+
+}  // namespace hofem

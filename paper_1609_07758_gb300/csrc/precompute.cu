@@ -112,6 +112,29 @@ static void gauss_legendre(int G, std::vector<dd>& xs, std::vector<dd>& ws) {
   }
 }
 
+// Load-vector quadrature of Sect. 2 par. 5: the (n+1) Gauss-Legendre points xi_g on
+// [-1, 1] (ascending) and T[a (n+1) + g] = w_g e_a(xi_g), rounded once from double-double.
+void element_load_table(int n, std::vector<double>* T, std::vector<double>* xi) {
+  const int m = n + 1, G = n + 1;
+  std::vector<dd> xs, ws;
+  gauss_legendre(G, xs, ws);
+  std::vector<dd> t(m);
+  for (int k = 0; k < m; ++k) t[k] = dd_make(-1.0) + dd_from_int_ratio(2 * k, n);
+  T->assign(m * G, 0.0);
+  xi->assign(G, 0.0);
+  // gauss_legendre returns the nodes in descending order (cos of increasing angles)
+  for (int g = 0; g < G; ++g) {
+    const int gs = G - 1 - g;
+    (*xi)[g] = dd_to_double(xs[gs]);
+    for (int a = 0; a < m; ++a) {
+      dd v = dd_make(1.0);
+      for (int q = 0; q < m; ++q)
+        if (q != a) v = v * (xs[gs] - t[q]) / (t[a] - t[q]);
+      (*T)[a * G + g] = dd_to_double(ws[gs] * v);
+    }
+  }
+}
+
 // A_ab = int e'_a e'_b, C_ab = int e_a e_b on [-1, 1], equispaced Lagrange basis.
 void element_matrices_dd(int n, std::vector<dd>& A, std::vector<dd>& C) {
   const int m = n + 1, G = n + 1;
