@@ -147,6 +147,18 @@ hofem_status hofem_quadrature_points(hofem_plan_t plan, int axis, double* x);
  * Asynchronous on stream; fq != fh. */
 hofem_status hofem_load(hofem_plan_t plan, const double* fq, double* fh, int nrhs, void* stream);
 
+/* out = (C_1 x .. x C_N) u, the matrix-free mass operator of Eq. bvp glob 2 (its alpha
+ * term with alpha = 1).  u, out: distinct device FP64 arrays (nrhs, M_1..M_N). */
+hofem_status hofem_mass(hofem_plan_t plan, const double* u, double* out, int nrhs, void* stream);
+
+/* Implicit (backward Euler) steps of the heat equation u_t - Lap u = g, the paper's stated
+ * application of the solver (Sect. 1; closing remarks of Sect. 2): with a plan built for
+ * alpha = 1/tau > 0, each step solves (A + alpha C x .. x C) u_new = alpha (C x .. x C) u
+ * + g^h (Eq. bvp glob 2) and overwrites u.  g: device FP64 (nrhs, M_1..M_N) in the f^h scaling, or NULL (g = 0).
+ * Refined plans run their fixed correction count per step (capturable in a CUDA graph
+ * after a first call has allocated the plan's step buffer).  Asynchronous on stream. */
+hofem_status hofem_heat_steps(hofem_plan_t plan, double* u, const double* g, int steps, int nrhs, void* stream);
+
 /* Autotuner: time every candidate launch shape (sweep lines per CTA W and DST batch J;
  * operator elements per CTA E) of this plan's solve and apply for nrhs right-hand sides
  * on its own workspace, and keep the fastest per shape in a process-wide table that

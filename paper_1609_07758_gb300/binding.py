@@ -24,7 +24,7 @@ EXPORTED = (
     "hofem_destroy", "hofem_status_string", "hofem_last_error", "hofem_profile", "hofem_get_profile",
     "hofem_apply_static", "hofem_autotune", "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve",
     "hofem_batch_get_info", "hofem_batch_get_plan", "hofem_batch_destroy", "hofem_quadrature_points",
-    "hofem_load",
+    "hofem_load", "hofem_mass", "hofem_heat_steps",
 )
 
 
@@ -98,6 +98,8 @@ def load_library():
     lib.hofem_autotune.argtypes = [P, I, V]
     lib.hofem_quadrature_points.argtypes = [P, I, ctypes.POINTER(D)]
     lib.hofem_load.argtypes = [P, V, V, I, V]
+    lib.hofem_mass.argtypes = [P, V, V, I, V]
+    lib.hofem_heat_steps.argtypes = [P, V, V, I, I, V]
     lib.hofem_batch_plan.argtypes = [I, ctypes.POINTER(hofem_problem), I, ctypes.POINTER(P)]
     lib.hofem_batch_tune.argtypes = [P, V]
     lib.hofem_batch_solve.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), V]
@@ -109,7 +111,8 @@ def load_library():
                  "hofem_residual", "hofem_transform1d", "hofem_get_eigen", "hofem_get_info",
                  "hofem_profile", "hofem_get_profile", "hofem_apply_static", "hofem_autotune",
                  "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve", "hofem_batch_get_info",
-                 "hofem_batch_get_plan", "hofem_quadrature_points", "hofem_load"):
+                 "hofem_batch_get_plan", "hofem_quadrature_points", "hofem_load", "hofem_mass",
+                 "hofem_heat_steps"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -278,6 +281,14 @@ class Plan:
                                                       x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                "hofem_quadrature_points")
         return x
+
+    def mass(self, u, out, nrhs, stream=None):
+        _check(load_library().hofem_mass(self.handle, _ptr(u), _ptr(out), int(nrhs), _stream(stream)), "hofem_mass")
+
+    def heat_steps(self, u, steps, nrhs, g=None, stream=None):
+        """Backward Euler steps of u_t - Lap u = g in place (plan alpha = 1 / tau)."""
+        _check(load_library().hofem_heat_steps(self.handle, _ptr(u), _ptr(g), int(steps), int(nrhs),
+                                               _stream(stream)), "hofem_heat_steps")
 
     def load(self, fq, fh, nrhs, stream=None):
         """fh = f^h from samples fq of f at the tensor product of the quadrature points."""

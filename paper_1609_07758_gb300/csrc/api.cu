@@ -74,6 +74,8 @@ struct hofem_plan_s {
   std::vector<double> load_T, load_xi;
   double* ld[2] = {nullptr, nullptr};
   size_t ld_count = 0;
+  double* heat = nullptr;        // right-hand side of the heat steps (nrhs x unknowns)
+  int heat_nrhs = 0;
   double* r64 = nullptr;         // residual
   double* tmp64[4] = {nullptr, nullptr, nullptr, nullptr};
   double* norms = nullptr;       // 2 per rhs
@@ -546,6 +548,22 @@ hofem_status operator_apply(hofem_plan_s* p, const double* u, const double* f, d
   return run_apply(p, 0, t[2], t[3], nullptr, out, f, sc[0], 0.0, nrhs, s);
 }
 
+
+// out = (C_1 x ... x C_N) u: operator sweeps with the stiffness coefficient 0, keeping
+// the mass product of each axis (the second output is scratch).
+hofem_status mass_apply(hofem_plan_s* p, const double* u, double* out, int nrhs, cudaStream_t s) {
+  hofem_status st = reserve(p, nrhs);
+  if (st != HOFEM_OK) return st;
+  double** t = p->tmp64;
+  if (p->N == 2) {
+    if ((st = run_apply(p, 1, u, nullptr, t[0], t[1], nullptr, 0.0, 0.0, nrhs, s)) != HOFEM_OK) return st;
+    return run_apply(p, 0, t[0], nullptr, out, t[1], nullptr, 0.0, 0.0, nrhs, s);
+  }
+  if ((st = run_apply(p, 2, u, nullptr, t[0], t[1], nullptr, 0.0, 0.0, nrhs, s)) != HOFEM_OK) return st;
+  if ((st = run_apply(p, 1, t[0], nullptr, t[2], t[1], nullptr, 0.0, 0.0, nrhs, s)) != HOFEM_OK) return st;
+  return run_apply(p, 0, t[2], nullptr, out, t[1], nullptr, 0.0, 0.0, nrhs, s);
+}
+
 }  // namespace
 
 namespace hofem {
@@ -935,6 +953,38 @@ hofem_status hofem_load(hofem_plan_t p, const double* fq, double* fh, int nrhs, 
   return HOFEM_OK;
 }
 
+hofem_status hofem_mass(hofem_plan_t p, const double* u, double* out, int nrhs, void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (!u || !out || nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or nrhs");
+  if ((const void*)u == (const void*)out) return fail(HOFEM_ERR_INVALID_ARG, "u and out must differ");
+  return mass_apply(p, u, out, nrhs, (cudaStream_t)stream);
+}
+
+hofem_status hofem_heat_steps(hofem_plan_t p, double* u, const double* g, int steps, int nrhs, void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (!u || nrhs < 1 || steps < 0) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers, nrhs or steps");
+  if (!(p->alpha > 0.0)) return fail(HOFEM_ERR_INVALID_ARG, "heat steps need a plan with alpha = 1/tau > 0");
+  if (g && (const void*)g == (const void*)u) return fail(HOFEM_ERR_INVALID_ARG, "g and u must differ");
+  cudaStream_t s = (cudaStream_t)stream;
+  hofem_status st = reserve(p, nrhs);
+  if (st != HOFEM_OK) return st;
+  if (nrhs > p->heat_nrhs) {
+    cudaFree(p->heat);
+    p->heat = nullptr;
+    p->heat_nrhs = 0;
+    HOFEM_CUDA(cudaMalloc(&p->heat, (size_t)nrhs * p->total * sizeof(double)), "cudaMalloc(heat rhs)");
+    p->heat_nrhs = nrhs;
+  }
+  const long long cnt = (long long)nrhs * p->total;
+  for (int m = 0; m < steps; ++m) {
+    if ((st = mass_apply(p, u, p->heat, nrhs, s)) != HOFEM_OK) return st;
+    HOFEM_CUDA(launch_axpby(p->heat, p->alpha, g, cnt, s), "axpby launch");
+    p->info.kernel_launches += 1;
+    if ((st = hofem_solve(p, p->heat, u, nrhs, stream)) != HOFEM_OK) return st;
+  }
+  return HOFEM_OK;
+}
+
 hofem_status hofem_autotune(hofem_plan_t p, int nrhs, void* stream) {
   if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
   if (nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "nrhs must be >= 1");
@@ -1097,6 +1147,7 @@ void hofem_destroy(hofem_plan_t p) {
   free_workspace(p);
   cudaFree(p->ld[0]);
   cudaFree(p->ld[1]);
+  cudaFree(p->heat);
   for (int i = 0; i < p->N; ++i) free_axis(p->ax[i]);
   delete p;
 }

@@ -54,7 +54,18 @@ template <int N> cudaError_t launch_n(const LoadParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+__global__ void axpby_kernel(double* __restrict__ y, double a, const double* __restrict__ g, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    y[i] = g ? fma(a, y[i], __ldg(g + i)) : a * y[i];
+}
+
 }  // namespace
+
+cudaError_t launch_axpby(double* y, double a, const double* g, long long count, cudaStream_t s) {
+  const long long blocks = std::min<long long>((count + 255) / 256, 152LL * 16);
+  axpby_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(y, a, g, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_load(const LoadParams& p, cudaStream_t s) {
   switch (p.n) {
