@@ -147,6 +147,17 @@ hofem_status hofem_quadrature_points(hofem_plan_t plan, int axis, double* x);
  * Asynchronous on stream; fq != fh. */
 hofem_status hofem_load(hofem_plan_t plan, const double* fq, double* fh, int nrhs, void* stream);
 
+/* Algorithm (b) of Sect. 2 par. 4 in FP64: the direct F_n-transforms along x_2..x_N, then
+ * for every mode of those axes the banded SPD system (4 h_1^-2 A_1 + sigma C_1) v = f
+ * along x_1 (sigma = the mode's eigenvalue sum + alpha), solved by static condensation of
+ * the element interiors and a tridiagonal nodal Schur system, then the inverse transforms.
+ * One correction with the FP64 matrix-free residual follows (the interior blocks of
+ * high-order elements are ill-conditioned).  The same discrete solution as hofem_solve
+ * (algorithm (a)); f, u as for hofem_solve (f != u).  Orders n <= 9 (HOFEM_ERR_UNSUPPORTED
+ * above: at n = 16 the condensed solve is no longer a contraction in FP64).
+ * Asynchronous on stream. */
+hofem_status hofem_solve_banded(hofem_plan_t plan, const double* f, double* u, int nrhs, void* stream);
+
 /* out = (C_1 x .. x C_N) u, the matrix-free mass operator of Eq. bvp glob 2 (its alpha
  * term with alpha = 1).  u, out: distinct device FP64 arrays (nrhs, M_1..M_N). */
 hofem_status hofem_mass(hofem_plan_t plan, const double* u, double* out, int nrhs, void* stream);

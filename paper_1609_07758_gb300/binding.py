@@ -24,7 +24,7 @@ EXPORTED = (
     "hofem_destroy", "hofem_status_string", "hofem_last_error", "hofem_profile", "hofem_get_profile",
     "hofem_apply_static", "hofem_autotune", "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve",
     "hofem_batch_get_info", "hofem_batch_get_plan", "hofem_batch_destroy", "hofem_quadrature_points",
-    "hofem_load", "hofem_mass", "hofem_heat_steps",
+    "hofem_load", "hofem_mass", "hofem_heat_steps", "hofem_solve_banded",
 )
 
 
@@ -99,6 +99,7 @@ def load_library():
     lib.hofem_quadrature_points.argtypes = [P, I, ctypes.POINTER(D)]
     lib.hofem_load.argtypes = [P, V, V, I, V]
     lib.hofem_mass.argtypes = [P, V, V, I, V]
+    lib.hofem_solve_banded.argtypes = [P, V, V, I, V]
     lib.hofem_heat_steps.argtypes = [P, V, V, I, I, V]
     lib.hofem_batch_plan.argtypes = [I, ctypes.POINTER(hofem_problem), I, ctypes.POINTER(P)]
     lib.hofem_batch_tune.argtypes = [P, V]
@@ -112,7 +113,7 @@ def load_library():
                  "hofem_profile", "hofem_get_profile", "hofem_apply_static", "hofem_autotune",
                  "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve", "hofem_batch_get_info",
                  "hofem_batch_get_plan", "hofem_quadrature_points", "hofem_load", "hofem_mass",
-                 "hofem_heat_steps"):
+                 "hofem_heat_steps", "hofem_solve_banded"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -281,6 +282,11 @@ class Plan:
                                                       x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                "hofem_quadrature_points")
         return x
+
+    def solve_banded(self, f, u, nrhs, stream=None):
+        """Algorithm (b): transforms along x_2..x_N, banded solves along x_1 (FP64)."""
+        _check(load_library().hofem_solve_banded(self.handle, _ptr(f), _ptr(u), int(nrhs), _stream(stream)),
+               "hofem_solve_banded")
 
     def mass(self, u, out, nrhs, stream=None):
         _check(load_library().hofem_mass(self.handle, _ptr(u), _ptr(out), int(nrhs), _stream(stream)), "hofem_mass")

@@ -29,6 +29,7 @@ struct AxisTables {
   //   E[r][t] = (M[r][t] + M[r][n-t]) / 2 (t < h),  E[r][mid] = M[r][mid],
   //   O[r][t] = (M[r][t] - M[r][n-t]) / 2 (r, t < h),
   // so (M w)_r = E_r + O_r and (M w)_{n-r} = E_r - O_r with the folded w.
+  std::vector<double> Aloc, Cloc;        // (n+1)^2 local stiffness and mass, FP64
   std::vector<double> CfE, CfO;          // mass, FP64   (hr x hr, h x h)
   // Stiffness: for n <= 9 the integer matrix D A (exact; lo parts zero, a_scale = 1/D),
   // else A as double-double hi + lo (a_scale = 1).

@@ -495,6 +495,13 @@ hofem_status build_axis_tables(int n, int K, double X, AxisTables* out, std::str
       goto cleanup;
     }
     out->a_scale = exact ? inv_D : 1.0;
+    // full local matrices rounded to FP64 (the banded solve of algorithm (b))
+    out->Aloc.resize(m1 * m1);
+    out->Cloc.resize(m1 * m1);
+    for (int i = 0; i < m1 * m1; ++i) {
+      out->Aloc[i] = dd_to_double(A[i]);
+      out->Cloc[i] = dd_to_double(C[i]);
+    }
     out->CfE.assign(hr * hr, 0.0);
     out->AfE.assign(hr * hr, 0.0);
     out->AfELo.assign(hr * hr, 0.0);
