@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the plan-time autotuner (built-in launch shapes)")
+    ap.add_argument("--extras", action="store_true",
+                    help="also time on-device f^h, algorithm (b) and a heat step at the same size")
     ap.add_argument("--elements", type=int, default=K_ELEM,
                     help="elements per axis (default 1024, the benchmark workload; smaller K for profiling)")
     args = ap.parse_args()
@@ -209,6 +211,33 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def extra_paths(hofem, torch, f, u, stream, args):
+    """ms per call of the widened paths at the benchmark size (CUDA events, after warm-up)."""
+    K2, X2 = [K_ELEM, K_ELEM], [X_LEN, X_LEN]
+    out = {}
+
+    def time_ms(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    p64 = hofem.Plan(2, K2, N_ORDER, X2, hofem.HOFEM_FP64)
+    G = K_ELEM * (N_ORDER + 1)
+    fq = torch.ones((1, G, G), dtype=torch.float64, device="cuda")
+    out["load_fh_ms"] = time_ms(lambda: p64.load(fq, u, 1, stream))
+    out["solve_banded_fp64_ms"] = time_ms(lambda: p64.solve_banded(f, u, 1, stream))
+    ph = hofem.Plan(2, K2, N_ORDER, X2, hofem.HOFEM_FP32_REFINED, alpha=100.0)
+    uh = f.clone()
+    out["heat_step_refined_ms"] = time_ms(lambda: ph.heat_steps(uh, 1, 1, stream=stream))
+    return out
+
+
 def e2e_time(plan, f_host, f, stream, args, world, torch):
     """ms per step through the C ABI from pinned host buffers: H2D f, solve, D2H u."""
     fh = torch.from_numpy(f_host).pin_memory()
@@ -309,6 +338,9 @@ def main():
         ms_e2e = float("nan")
     else:
         ms_e2e = e2e_time(plan, f_host, f, stream, args, world, torch)
+    extras = None
+    if args.extras:
+        extras = extra_paths(hofem, torch, f, u, stream, args)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -360,6 +392,7 @@ def main():
         "e2e": None if args.no_e2e else {"value": job_throughput(UNKNOWNS, world, ms_e2e), "unit": UNIT,
                                          "h2d_bytes_per_step": 8 * UNKNOWNS, "d2h_bytes_per_step": 8 * UNKNOWNS},
         "gpu_launches": launches,
+        **({"extras_ms": extras} if extras else {}),
         "clocks": clock_info,
     }
     if rank == 0:
