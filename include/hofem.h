@@ -84,6 +84,7 @@ typedef struct {
   int threads_per_cta;
   long long kernel_launches; /* kernels this plan has launched since it was created */
   long long tuned_shapes;   /* launch-shape candidates measured by hofem_autotune */
+  int orders[3];            /* element order per axis (n above is their maximum) */
 } hofem_info;
 
 /* One problem of a batch: N = 2 or 3 axes with K[i] elements of length X[i] (entries
@@ -128,6 +129,12 @@ typedef struct {
 hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, double alpha,
                         hofem_plan_t* out);
 
+/* hofem_plan with an element order n[i] per axis (the paper allows n_i per axis, Sect. 2
+ * par. 4): M_i = n_i K_i - 1, each axis' eigen-data, transforms and operator products of
+ * its own order. */
+hofem_status hofem_plan_orders(int N, const int* K, const int* n, const double* X, int dtype, double alpha,
+                               hofem_plan_t* out);
+
 /* Refined dtypes only: iters = residual/correction steps after the first low-precision
  * solve (0..100; default FP32 2 when every K is a power of two, else 3; BF16 and FP16 8); tol > 0 additionally stops early once ||delta||/||u|| <= tol,
  * which synchronises the stream once per step.  tol = 0 keeps a fixed count (capturable). */
@@ -153,7 +160,7 @@ hofem_status hofem_load(hofem_plan_t plan, const double* fq, double* fh, int nrh
  * the element interiors and a tridiagonal nodal Schur system, then the inverse transforms.
  * One correction with the FP64 matrix-free residual follows (the interior blocks of
  * high-order elements are ill-conditioned).  The same discrete solution as hofem_solve
- * (algorithm (a)); f, u as for hofem_solve (f != u).  Orders n <= 9 (HOFEM_ERR_UNSUPPORTED
+ * (algorithm (a)); f, u as for hofem_solve (f != u).  Orders n_1 <= 9 (HOFEM_ERR_UNSUPPORTED
  * above: at n = 16 the condensed solve is no longer a contraction in FP64).
  * Asynchronous on stream. */
 hofem_status hofem_solve_banded(hofem_plan_t plan, const double* f, double* u, int nrhs, void* stream);

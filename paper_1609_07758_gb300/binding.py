@@ -24,7 +24,7 @@ EXPORTED = (
     "hofem_destroy", "hofem_status_string", "hofem_last_error", "hofem_profile", "hofem_get_profile",
     "hofem_apply_static", "hofem_autotune", "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve",
     "hofem_batch_get_info", "hofem_batch_get_plan", "hofem_batch_destroy", "hofem_quadrature_points",
-    "hofem_load", "hofem_mass", "hofem_heat_steps", "hofem_solve_banded",
+    "hofem_load", "hofem_mass", "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders",
 )
 
 
@@ -42,6 +42,7 @@ class hofem_info(ctypes.Structure):
         ("table_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
         ("lines_per_cta", ctypes.c_int * 3), ("threads_per_cta", ctypes.c_int),
         ("kernel_launches", ctypes.c_longlong), ("tuned_shapes", ctypes.c_longlong),
+        ("orders", ctypes.c_int * 3),
     ]
 
 
@@ -78,6 +79,8 @@ def load_library():
     lib = ctypes.CDLL(path)
     P, I, D, L, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long, ctypes.c_void_p
     lib.hofem_plan.argtypes = [I, ctypes.POINTER(I), I, ctypes.POINTER(D), I, D, ctypes.POINTER(P)]
+    lib.hofem_plan_orders.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), I, D,
+                                      ctypes.POINTER(P)]
     lib.hofem_set_refinement.argtypes = [P, I, D]
     lib.hofem_reserve.argtypes = [P, I]
     lib.hofem_solve.argtypes = [P, V, V, I, V]
@@ -113,7 +116,7 @@ def load_library():
                  "hofem_profile", "hofem_get_profile", "hofem_apply_static", "hofem_autotune",
                  "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve", "hofem_batch_get_info",
                  "hofem_batch_get_plan", "hofem_quadrature_points", "hofem_load", "hofem_mass",
-                 "hofem_heat_steps", "hofem_solve_banded"):
+                 "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -162,11 +165,17 @@ def _stream(s):
 
 
 def hofem_plan(N, K, n, X, dtype=HOFEM_FP64, alpha=0.0):
+    """n: one order for every axis, or a sequence of N orders (hofem_plan_orders)."""
     lib = load_library()
     out = ctypes.c_void_p()
     Ka = (ctypes.c_int * N)(*[int(k) for k in K])
     Xa = (ctypes.c_double * N)(*[float(x) for x in X])
-    _check(lib.hofem_plan(int(N), Ka, int(n), Xa, int(dtype), float(alpha), ctypes.byref(out)), "hofem_plan")
+    if isinstance(n, (list, tuple)):
+        Na = (ctypes.c_int * N)(*[int(v) for v in n])
+        _check(lib.hofem_plan_orders(int(N), Ka, Na, Xa, int(dtype), float(alpha), ctypes.byref(out)),
+               "hofem_plan_orders")
+    else:
+        _check(lib.hofem_plan(int(N), Ka, int(n), Xa, int(dtype), float(alpha), ctypes.byref(out)), "hofem_plan")
     return out.value
 
 
@@ -248,7 +257,8 @@ class Plan:
     def __init__(self, N, K, n, X, dtype=HOFEM_FP64, alpha=0.0):
         self.handle = hofem_plan(N, K, n, X, dtype, alpha)
         self.N, self.K, self.n, self.X, self.dtype, self.alpha = N, list(K), n, list(X), dtype, alpha
-        self.M = [n * k - 1 for k in K]
+        self.ns = list(n) if isinstance(n, (list, tuple)) else [n] * N
+        self.M = [nn * k - 1 for nn, k in zip(self.ns, K)]
 
     def solve(self, f, u, nrhs, stream=None):
         hofem_solve(self.handle, f, u, nrhs, stream)
@@ -277,7 +287,7 @@ class Plan:
     def quadrature_points(self, axis):
         """The K (n+1) Gauss-Legendre points of the load vector along `axis` (numpy)."""
         import numpy as np
-        x = np.zeros(self.K[axis] * (self.n + 1))
+        x = np.zeros(self.K[axis] * (self.ns[axis] + 1))
         _check(load_library().hofem_quadrature_points(self.handle, int(axis),
                                                       x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                "hofem_quadrature_points")

@@ -72,7 +72,7 @@ struct hofem_plan_s {
   unsigned long long* amax = nullptr;   // per-rhs max |rhs| (FP16 work arrays only)
   int amax_exp = 10;             // FP16: scaled right-hand sides have |max| in [2^(e-1), 2^e)
   // load-vector quadrature (hofem_load): tables and the two intermediate axis buffers
-  std::vector<double> load_T, load_xi;
+  std::vector<double> load_T[3], load_xi[3];   // per axis
   double* ld[2] = {nullptr, nullptr};
   size_t ld_count = 0;
   double* heat = nullptr;        // right-hand side of the heat steps (nrhs x unknowns)
@@ -767,7 +767,7 @@ hofem_status tune_plan(hofem_plan_s* p, int nrhs, cudaStream_t s, int* measured)
     double best = 1e30;
     int bE = 0;
     for (int E : {4, 8, 16, 32}) {
-      if (E > p->ax[ap.axis].h.K || apply_smem_bytes(p->n, E) > kSmemLimit) continue;
+      if (E > p->ax[ap.axis].h.K || apply_smem_bytes(p->ax[ap.axis].h.n, E) > kSmemLimit) continue;
       g_force_a = E;
       bool ok = false;
       const double ms = time_launches(s, [&]() {
@@ -809,12 +809,22 @@ const char* hofem_status_string(int s) {
 const char* hofem_last_error(void) { return g_last_error.c_str(); }
 
 hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, double alpha, hofem_plan_t* out) {
+  const int ns[3] = {n, n, n};
+  return hofem_plan_orders(N, K, ns, X, dtype, alpha, out);
+}
+
+hofem_status hofem_plan_orders(int N, const int* K, const int* ns, const double* X, int dtype, double alpha,
+                               hofem_plan_t* out) {
   auto t0 = std::chrono::steady_clock::now();
   if (!out) return fail(HOFEM_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (N != 2 && N != 3) return fail(HOFEM_ERR_INVALID_ARG, "N must be 2 or 3");
-  if (!K || !X) return fail(HOFEM_ERR_INVALID_ARG, "K or X is NULL");
-  if (n < 1 || n > kMaxN) return fail(HOFEM_ERR_INVALID_ARG, "order n must be in 1..16");
+  if (!K || !X || !ns) return fail(HOFEM_ERR_INVALID_ARG, "K, n or X is NULL");
+  int n = 0;                                     // largest order over the axes
+  for (int i = 0; i < N; ++i) {
+    if (ns[i] < 1 || ns[i] > kMaxN) return fail(HOFEM_ERR_INVALID_ARG, "order n must be in 1..16");
+    n = std::max(n, ns[i]);
+  }
   if (dtype < HOFEM_FP64 || dtype > HOFEM_FP16_REFINED) return fail(HOFEM_ERR_UNSUPPORTED, "unknown dtype");
   double lam_bound = 0.0;
   for (int i = 0; i < N; ++i) {
@@ -852,7 +862,7 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
   for (int i = 0; i < N; ++i) {
     p->K[i] = K[i];
     p->X[i] = X[i];
-    p->M[i] = n * K[i] - 1;
+    p->M[i] = ns[i] * K[i] - 1;
     p->total *= p->M[i];
   }
   hofem_status st = HOFEM_OK;
@@ -861,21 +871,21 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
     std::string err;
     int same = -1;
     for (int j = 0; j < i; ++j)
-      if (K[j] == K[i] && X[j] == X[i]) same = j;
+      if (K[j] == K[i] && X[j] == X[i] && ns[j] == ns[i]) same = j;
     if (same >= 0) {
       a.h = p->ax[same].h;
     } else {
-      st = build_axis_tables(n, K[i], X[i], &a.h, &err);
+      st = build_axis_tables(ns[i], K[i], X[i], &a.h, &err);
       if (st != HOFEM_OK) { g_last_error = err; break; }
     }
     size_t& tb = p->table_bytes;
     if ((st = upload(a.h.lam, &a.lam64, &tb)) != HOFEM_OK) break;
     {
       // mixing rows padded to a multiple of 4 entries for 16-byte vector loads
-      const int np = (n + 3) & ~3;
-      std::vector<double> padded((size_t)(K[i] - 1) * n * np, 0.0);
-      for (size_t r = 0; r < (size_t)(K[i] - 1) * n; ++r)
-        for (int c = 0; c < n; ++c) padded[r * np + c] = a.h.mix[r * n + c];
+      const int na = ns[i], np = (na + 3) & ~3;
+      std::vector<double> padded((size_t)(K[i] - 1) * na * np, 0.0);
+      for (size_t r = 0; r < (size_t)(K[i] - 1) * na; ++r)
+        for (int c = 0; c < na; ++c) padded[r * np + c] = a.h.mix[r * na + c];
       a.mixNP = np;
       if ((st = upload(padded, &a.mix64, &tb)) != HOFEM_OK) break;
       if ((st = upload(padded, &a.mix32, &tb)) != HOFEM_OK) break;
@@ -905,10 +915,11 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
   p->refine_iters = dtype == HOFEM_FP32_REFINED                                    ? (all_pow2 ? 2 : 3)
                     : (dtype == HOFEM_BF16_REFINED || dtype == HOFEM_FP16_REFINED) ? 8
                                                                                     : 0;
-  element_load_table(n, &p->load_T, &p->load_xi);
+  for (int i = 0; i < N; ++i) element_load_table(ns[i], &p->load_T[i], &p->load_xi[i]);
   hofem_info& inf = p->info;
   inf.N = N;
   inf.n = n;
+  for (int i = 0; i < N; ++i) inf.orders[i] = ns[i];
   for (int i = 0; i < N; ++i) {
     inf.K[i] = K[i];
     inf.M[i] = p->M[i];
@@ -935,10 +946,10 @@ hofem_status hofem_set_refinement(hofem_plan_t p, int iters, double tol) {
 hofem_status hofem_quadrature_points(hofem_plan_t p, int axis, double* x) {
   if (!p || !x) return fail(HOFEM_ERR_INVALID_ARG, "plan or x is NULL");
   if (axis < 0 || axis >= p->N) return fail(HOFEM_ERR_INVALID_ARG, "axis out of range");
-  const int G = p->n + 1, K = p->K[axis];
+  const int G = p->ax[axis].h.n + 1, K = p->K[axis];
   const double h = p->X[axis] / K;
   for (int e = 0; e < K; ++e)
-    for (int g = 0; g < G; ++g) x[(size_t)e * G + g] = e * h + (p->load_xi[g] + 1.0) * h / 2.0;
+    for (int g = 0; g < G; ++g) x[(size_t)e * G + g] = e * h + (p->load_xi[axis][g] + 1.0) * h / 2.0;
   return HOFEM_OK;
 }
 
@@ -947,9 +958,9 @@ hofem_status hofem_load(hofem_plan_t p, const double* fq, double* fh, int nrhs, 
   if (!fq || !fh || nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or nrhs");
   if ((const void*)fq == (const void*)fh) return fail(HOFEM_ERR_INVALID_ARG, "fq and fh must differ");
   cudaStream_t s = (cudaStream_t)stream;
-  const int N = p->N, n = p->n, G = n + 1;
+  const int N = p->N;
   long long L[3];                                   // current length of every axis
-  for (int i = 0; i < N; ++i) L[i] = (long long)p->K[i] * G;
+  for (int i = 0; i < N; ++i) L[i] = (long long)p->K[i] * (p->ax[i].h.n + 1);
   // intermediates after axes N-1 .. 1 (axis 0 writes fh)
   size_t need = 0;
   {
@@ -971,11 +982,12 @@ hofem_status hofem_load(hofem_plan_t p, const double* fq, double* fh, int nrhs, 
     p->ld_count = need;
   }
   LoadParams P{};
-  P.n = n;
-  for (int i = 0; i < G * G; ++i) P.T[i] = p->load_T[i];
   const double* in = fq;
   int buf = 0;
   for (int a = N - 1; a >= 0; --a) {
+    const int na = p->ax[a].h.n, G = na + 1;
+    P.n = na;
+    for (int i = 0; i < G * G; ++i) P.T[i] = p->load_T[a][i];
     P.in = in;
     P.out = a == 0 ? fh : p->ld[buf];
     P.K = p->K[a];
@@ -997,8 +1009,8 @@ hofem_status hofem_solve_banded(hofem_plan_t p, const double* f, double* u, int 
   if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
   if (!f || !u || nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or nrhs");
   if ((const void*)f == (const void*)u) return fail(HOFEM_ERR_INVALID_ARG, "f and u must differ");
-  if (p->n > kExactStiffnessMaxN)
-    return fail(HOFEM_ERR_UNSUPPORTED, "algorithm (b) supports n <= 9 (higher orders: use hofem_solve)");
+  if (p->ax[0].h.n > kExactStiffnessMaxN)
+    return fail(HOFEM_ERR_UNSUPPORTED, "algorithm (b) supports n_1 <= 9 (higher orders: use hofem_solve)");
   cudaStream_t s = (cudaStream_t)stream;
   hofem_status st = reserve(p, nrhs);
   if (st != HOFEM_OK) return st;

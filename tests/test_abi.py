@@ -55,6 +55,17 @@ def test_invalid_arguments_are_rejected_on_the_host(lib, N, K, n, X, dtype, alph
     assert st == 1 and not out.value
 
 
+def test_per_axis_orders_are_checked_on_the_host(lib):
+    out = ctypes.c_void_p()
+    lib.hofem_plan_orders.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int, ctypes.c_double, ctypes.c_void_p]
+    Ks = (ctypes.c_int * 2)(8, 8)
+    Xs = (ctypes.c_double * 2)(1.0, 1.0)
+    for ns in ((2, 0), (17, 3)):
+        assert lib.hofem_plan_orders(2, Ks, (ctypes.c_int * 2)(*ns), Xs, 0, 0.0, ctypes.byref(out)) == 1
+    assert lib.hofem_plan_orders(2, Ks, None, Xs, 0, 0.0, ctypes.byref(out)) == 1
+
+
 def test_unsupported_shapes_and_dtypes(lib):
     out = ctypes.c_void_p()
     Ks = (ctypes.c_int * 2)(16384, 8)        # K above 8192
