@@ -835,11 +835,18 @@ hofem_status hofem_plan_orders(int N, const int* K, const int* ns, const double*
   }
   if (!(alpha > -lam_bound) || !std::isfinite(alpha))
     return fail(HOFEM_ERR_INVALID_ARG, "alpha must exceed -pi^2 sum X_i^-2");
-  static bool limits_set = false;
-  if (!limits_set) {
-    HOFEM_CUDA(sweep_set_smem_limits(), "cudaFuncSetAttribute(sweep)");
-    HOFEM_CUDA(apply_set_smem_limits(), "cudaFuncSetAttribute(apply)");
-    limits_set = true;
+  {
+    // the dynamic shared-memory opt-in is a per-device function attribute
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    HOFEM_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(done.begin(), done.end(), dev) == done.end()) {
+      HOFEM_CUDA(sweep_set_smem_limits(), "cudaFuncSetAttribute(sweep)");
+      HOFEM_CUDA(apply_set_smem_limits(), "cudaFuncSetAttribute(apply)");
+      done.push_back(dev);
+    }
   }
   hofem_plan_s* p = new hofem_plan_s();
   p->N = N;
