@@ -165,6 +165,23 @@ hofem_status hofem_load(hofem_plan_t plan, const double* fq, double* fh, int nrh
  * Asynchronous on stream. */
 hofem_status hofem_solve_banded(hofem_plan_t plan, const double* f, double* u, int nrhs, void* stream);
 
+/* r = A_a u for the variable-coefficient problem -div(a grad u) = f on the plan's 2D mesh
+ * (one order n <= 9 on both axes), in the scaling of Eq. bvp glob 2: per element
+ * (2/h_1)(2/h_2) int a grad phi_p . grad phi_q by the (n+1)-point Gauss-Legendre rule per
+ * direction (Sect. 2 par. 5).  aq: device FP64 (K_1 (n+1), K_2 (n+1)), the values of a > 0
+ * at the points of hofem_quadrature_points; u, r: device FP64 (M_1, M_2), distinct.  For
+ * a = 1 this is hofem_apply with alpha = 0.  Asynchronous on stream. */
+hofem_status hofem_apply_varcoef(hofem_plan_t plan, const double* aq, const double* u, double* r, void* stream);
+
+/* The solver as a preconditioner (Sect. 1): conjugate gradients on A_a u = f (see
+ * hofem_apply_varcoef) preconditioned by the plan's constant-coefficient solve (build
+ * the plan with alpha = 0).  u: initial guess in, solution out; stops when
+ * ||f - A_a u||_2 <= tol ||f||_2 or after maxit steps (HOFEM_ERR_NOT_CONVERGED).  iters and
+ * relres (HOST, may be NULL) receive the steps taken and the final relative residual.
+ * Synchronises the stream three times per step (dot products). */
+hofem_status hofem_pcg(hofem_plan_t plan, const double* aq, const double* f, double* u, double tol, int maxit,
+                       int* iters, double* relres, void* stream);
+
 /* out = (C_1 x .. x C_N) u, the matrix-free mass operator of Eq. bvp glob 2 (its alpha
  * term with alpha = 1).  u, out: distinct device FP64 arrays (nrhs, M_1..M_N). */
 hofem_status hofem_mass(hofem_plan_t plan, const double* u, double* out, int nrhs, void* stream);

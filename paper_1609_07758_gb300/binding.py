@@ -25,6 +25,7 @@ EXPORTED = (
     "hofem_apply_static", "hofem_autotune", "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve",
     "hofem_batch_get_info", "hofem_batch_get_plan", "hofem_batch_destroy", "hofem_quadrature_points",
     "hofem_load", "hofem_mass", "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders",
+    "hofem_apply_varcoef", "hofem_pcg",
 )
 
 
@@ -103,6 +104,8 @@ def load_library():
     lib.hofem_load.argtypes = [P, V, V, I, V]
     lib.hofem_mass.argtypes = [P, V, V, I, V]
     lib.hofem_solve_banded.argtypes = [P, V, V, I, V]
+    lib.hofem_apply_varcoef.argtypes = [P, V, V, V, V]
+    lib.hofem_pcg.argtypes = [P, V, V, V, D, I, ctypes.POINTER(I), ctypes.POINTER(D), V]
     lib.hofem_heat_steps.argtypes = [P, V, V, I, I, V]
     lib.hofem_batch_plan.argtypes = [I, ctypes.POINTER(hofem_problem), I, ctypes.POINTER(P)]
     lib.hofem_batch_tune.argtypes = [P, V]
@@ -116,7 +119,8 @@ def load_library():
                  "hofem_profile", "hofem_get_profile", "hofem_apply_static", "hofem_autotune",
                  "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve", "hofem_batch_get_info",
                  "hofem_batch_get_plan", "hofem_quadrature_points", "hofem_load", "hofem_mass",
-                 "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders"):
+                 "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders", "hofem_apply_varcoef",
+                 "hofem_pcg"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -297,6 +301,17 @@ class Plan:
         """Algorithm (b): transforms along x_2..x_N, banded solves along x_1 (FP64)."""
         _check(load_library().hofem_solve_banded(self.handle, _ptr(f), _ptr(u), int(nrhs), _stream(stream)),
                "hofem_solve_banded")
+
+    def apply_varcoef(self, aq, u, r, stream=None):
+        _check(load_library().hofem_apply_varcoef(self.handle, _ptr(aq), _ptr(u), _ptr(r), _stream(stream)),
+               "hofem_apply_varcoef")
+
+    def pcg(self, aq, f, u, tol=1e-10, maxit=100, stream=None):
+        """CG on -div(a grad u) = f preconditioned by this plan's solve; returns (iters, relres)."""
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        _check(load_library().hofem_pcg(self.handle, _ptr(aq), _ptr(f), _ptr(u), float(tol), int(maxit),
+                                        ctypes.byref(it), ctypes.byref(rr), _stream(stream)), "hofem_pcg")
+        return it.value, rr.value
 
     def mass(self, u, out, nrhs, stream=None):
         _check(load_library().hofem_mass(self.handle, _ptr(u), _ptr(out), int(nrhs), _stream(stream)), "hofem_mass")

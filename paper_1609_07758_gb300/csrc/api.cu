@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "banded.cuh"
+#include "varcoef.cuh"
 #include "load.cuh"
 #include "residual.cuh"
 #include "sweep.cuh"
@@ -77,6 +78,11 @@ struct hofem_plan_s {
   size_t ld_count = 0;
   double* heat = nullptr;        // right-hand side of the heat steps (nrhs x unknowns)
   int heat_nrhs = 0;
+  // variable-coefficient operator and PCG: device basis tables, r z p q vectors, dot slot
+  double *vcB = nullptr, *vcD = nullptr, *vcW = nullptr;
+  double* cg[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* dot = nullptr;
+  double* h_dot = nullptr;
   double* r64 = nullptr;         // residual
   double* tmp64[4] = {nullptr, nullptr, nullptr, nullptr};
   double* norms = nullptr;       // 2 per rhs
@@ -604,6 +610,53 @@ hofem_status banded_once(hofem_plan_s* p, const double* f, double* u, int nrhs, 
   return HOFEM_OK;
 }
 
+
+// Variable-coefficient operator r = A_a u (2D, equal orders): tables uploaded on first use.
+hofem_status varcoef_apply(hofem_plan_s* p, const double* aq, const double* u, double* r, cudaStream_t s) {
+  if (p->N != 2 || p->ax[0].h.n != p->ax[1].h.n || p->ax[0].h.n > 9)
+    return fail(HOFEM_ERR_UNSUPPORTED, "the variable-coefficient operator is 2D with one order n <= 9");
+  const int n = p->ax[0].h.n, G = n + 1;
+  if (!p->vcB) {
+    std::vector<double> B, D, w;
+    element_basis_tables(n, &B, &D, &w);
+    size_t tb = 0;
+    hofem_status st;
+    if ((st = upload(B, &p->vcB, &tb)) != HOFEM_OK) return st;
+    if ((st = upload(D, &p->vcD, &tb)) != HOFEM_OK) return st;
+    if ((st = upload(w, &p->vcW, &tb)) != HOFEM_OK) return st;
+  }
+  VarcoefParams V{};
+  V.u = u;
+  V.r = r;
+  V.aq = aq;
+  V.B = p->vcB;
+  V.D = p->vcD;
+  V.w = p->vcW;
+  V.K0 = p->K[0];
+  V.K1 = p->K[1];
+  V.M0 = p->M[0];
+  V.M1 = p->M[1];
+  V.n = n;
+  V.s0 = 4.0 * (double)p->K[0] * (double)p->K[0] / (p->X[0] * p->X[0]);
+  V.s1 = 4.0 * (double)p->K[1] * (double)p->K[1] / (p->X[1] * p->X[1]);
+  (void)G;
+  HOFEM_CUDA(cudaMemsetAsync(r, 0, (size_t)p->total * sizeof(double), s), "memset (varcoef)");
+  HOFEM_CUDA(launch_varcoef(V, s), "varcoef launch");
+  p->info.kernel_launches += 1;
+  return HOFEM_OK;
+}
+
+// x . y on the device, returned to the host (synchronises s).
+hofem_status device_dot(hofem_plan_s* p, const double* x, const double* y, cudaStream_t s, double* out) {
+  HOFEM_CUDA(cudaMemsetAsync(p->dot, 0, sizeof(double), s), "memset (dot)");
+  HOFEM_CUDA(launch_dot(x, y, p->total, p->dot, s), "dot launch");
+  HOFEM_CUDA(cudaMemcpyAsync(p->h_dot, p->dot, sizeof(double), cudaMemcpyDeviceToHost, s), "copy (dot)");
+  HOFEM_CUDA(cudaStreamSynchronize(s), "stream sync (dot)");
+  p->info.kernel_launches += 1;
+  *out = *p->h_dot;
+  return HOFEM_OK;
+}
+
 }  // namespace
 
 namespace hofem {
@@ -1033,6 +1086,62 @@ hofem_status hofem_solve_banded(hofem_plan_t p, const double* f, double* u, int 
   return HOFEM_OK;
 }
 
+hofem_status hofem_apply_varcoef(hofem_plan_t p, const double* aq, const double* u, double* r, void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (!aq || !u || !r || (const void*)u == (const void*)r) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers");
+  return varcoef_apply(p, aq, u, r, (cudaStream_t)stream);
+}
+
+hofem_status hofem_pcg(hofem_plan_t p, const double* aq, const double* f, double* u, double tol, int maxit,
+                       int* iters, double* relres, void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (!aq || !f || !u || (const void*)f == (const void*)u) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers");
+  if (!(tol > 0.0) || maxit < 1) return fail(HOFEM_ERR_INVALID_ARG, "tol > 0 and maxit >= 1 required");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t cnt = (size_t)p->total;
+  for (double*& v : p->cg)
+    if (!v) HOFEM_CUDA(cudaMalloc(&v, cnt * sizeof(double)), "cudaMalloc(pcg vectors)");
+  if (!p->dot) HOFEM_CUDA(cudaMalloc(&p->dot, sizeof(double)), "cudaMalloc(dot)");
+  if (!p->h_dot) HOFEM_CUDA(cudaMallocHost(&p->h_dot, sizeof(double)), "cudaMallocHost(dot)");
+  double *r = p->cg[0], *z = p->cg[1], *d = p->cg[2], *q = p->cg[3];
+  hofem_status st;
+  // r = f - A_a u; z = P^-1 r (the fast constant-coefficient solve); d = z
+  if ((st = varcoef_apply(p, aq, u, r, s)) != HOFEM_OK) return st;
+  HOFEM_CUDA(launch_axpby(r, -1.0, f, (long long)cnt, s), "axpby launch");
+  double ff, rz, rr;
+  if ((st = device_dot(p, f, f, s, &ff)) != HOFEM_OK) return st;
+  if ((st = device_dot(p, r, r, s, &rr)) != HOFEM_OK) return st;
+  const double fn = std::sqrt(ff) > 0 ? std::sqrt(ff) : 1.0;
+  int k = 0;
+  double res = std::sqrt(rr) / fn;
+  if (res > tol) {
+    if ((st = hofem_solve(p, r, z, 1, stream)) != HOFEM_OK) return st;
+    HOFEM_CUDA(cudaMemcpyAsync(d, z, cnt * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy (pcg)");
+    if ((st = device_dot(p, r, z, s, &rz)) != HOFEM_OK) return st;
+    while (k < maxit) {
+      ++k;
+      if ((st = varcoef_apply(p, aq, d, q, s)) != HOFEM_OK) return st;
+      double dq;
+      if ((st = device_dot(p, d, q, s, &dq)) != HOFEM_OK) return st;
+      const double a = rz / dq;
+      HOFEM_CUDA(launch_axpy(u, a, d, (long long)cnt, s), "axpy launch");
+      HOFEM_CUDA(launch_axpy(r, -a, q, (long long)cnt, s), "axpy launch");
+      if ((st = device_dot(p, r, r, s, &rr)) != HOFEM_OK) return st;
+      res = std::sqrt(rr) / fn;
+      if (res <= tol) break;
+      if ((st = hofem_solve(p, r, z, 1, stream)) != HOFEM_OK) return st;
+      double rz_new;
+      if ((st = device_dot(p, r, z, s, &rz_new)) != HOFEM_OK) return st;
+      HOFEM_CUDA(launch_axpby(d, rz_new / rz, z, (long long)cnt, s), "axpby launch");
+      rz = rz_new;
+    }
+  }
+  if (iters) *iters = k;
+  if (relres) *relres = res;
+  if (res > tol) return fail(HOFEM_ERR_NOT_CONVERGED, "PCG reached maxit before the tolerance");
+  return HOFEM_OK;
+}
+
 hofem_status hofem_mass(hofem_plan_t p, const double* u, double* out, int nrhs, void* stream) {
   if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
   if (!u || !out || nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or nrhs");
@@ -1228,6 +1337,12 @@ void hofem_destroy(hofem_plan_t p) {
   cudaFree(p->ld[0]);
   cudaFree(p->ld[1]);
   cudaFree(p->heat);
+  cudaFree(p->vcB);
+  cudaFree(p->vcD);
+  cudaFree(p->vcW);
+  for (double* v : p->cg) cudaFree(v);
+  cudaFree(p->dot);
+  if (p->h_dot) cudaFreeHost(p->h_dot);
   for (int i = 0; i < p->N; ++i) free_axis(p->ax[i]);
   delete p;
 }

@@ -42,5 +42,7 @@ hofem_status build_axis_tables(int n, int K, double X, AxisTables* out, std::str
 
 // (n+1)-point Gauss-Legendre nodes xi (ascending) and T[a (n+1) + g] = w_g e_a(xi_g).
 void element_load_table(int n, std::vector<double>* T, std::vector<double>* xi);
+// B[g][a] = e_a(xi_g), D[g][a] = e_a'(xi_g) and the weights w_g of that rule.
+void element_basis_tables(int n, std::vector<double>* B, std::vector<double>* D, std::vector<double>* w);
 
 }  // namespace hofem

@@ -59,7 +59,18 @@ __global__ void axpby_kernel(double* __restrict__ y, double a, const double* __r
     y[i] = g ? fma(a, y[i], __ldg(g + i)) : a * y[i];
 }
 
+__global__ void axpy_kernel(double* __restrict__ y, double c, const double* __restrict__ x, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(c, __ldg(x + i), y[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_axpy(double* y, double c, const double* x, long long count, cudaStream_t s) {
+  const long long blocks = std::min<long long>((count + 255) / 256, 152LL * 16);
+  axpy_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(y, c, x, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_axpby(double* y, double a, const double* g, long long count, cudaStream_t s) {
   const long long blocks = std::min<long long>((count + 255) / 256, 152LL * 16);

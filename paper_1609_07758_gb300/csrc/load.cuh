@@ -17,5 +17,7 @@ struct LoadParams {
 cudaError_t launch_load(const LoadParams& p, cudaStream_t s);
 // y = a y + g (g may be null: y = a y), count doubles
 cudaError_t launch_axpby(double* y, double a, const double* g, long long count, cudaStream_t s);
+// y += c x
+cudaError_t launch_axpy(double* y, double c, const double* x, long long count, cudaStream_t s);
 
 }  // namespace hofem

@@ -135,6 +135,37 @@ void element_load_table(int n, std::vector<double>* T, std::vector<double>* xi) 
   }
 }
 
+// Basis and derivative values at the (n+1) Gauss-Legendre points (ascending) and the
+// weights: B[g (n+1) + a] = e_a(xi_g), D[g (n+1) + a] = e_a'(xi_g), rounded from double-double.
+void element_basis_tables(int n, std::vector<double>* B, std::vector<double>* D, std::vector<double>* w) {
+  const int m = n + 1, G = n + 1;
+  std::vector<dd> xs, ws;
+  gauss_legendre(G, xs, ws);
+  std::vector<dd> t(m);
+  for (int k = 0; k < m; ++k) t[k] = dd_make(-1.0) + dd_from_int_ratio(2 * k, n);
+  B->assign(G * m, 0.0);
+  D->assign(G * m, 0.0);
+  w->assign(G, 0.0);
+  for (int g = 0; g < G; ++g) {
+    const int gs = G - 1 - g;                    // gauss_legendre returns descending nodes
+    (*w)[g] = dd_to_double(ws[gs]);
+    for (int a = 0; a < m; ++a) {
+      dd v = dd_make(1.0), d = dd_make(0.0);
+      for (int q = 0; q < m; ++q)
+        if (q != a) v = v * (xs[gs] - t[q]) / (t[a] - t[q]);
+      for (int q = 0; q < m; ++q) {
+        if (q == a) continue;
+        dd term = dd_make(1.0) / (t[a] - t[q]);
+        for (int r = 0; r < m; ++r)
+          if (r != a && r != q) term = term * (xs[gs] - t[r]) / (t[a] - t[r]);
+        d = d + term;
+      }
+      (*B)[g * m + a] = dd_to_double(v);
+      (*D)[g * m + a] = dd_to_double(d);
+    }
+  }
+}
+
 // A_ab = int e'_a e'_b, C_ab = int e_a e_b on [-1, 1], equispaced Lagrange basis.
 void element_matrices_dd(int n, std::vector<dd>& A, std::vector<dd>& C) {
   const int m = n + 1, G = n + 1;
