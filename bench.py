@@ -235,6 +235,21 @@ def extra_paths(hofem, torch, f, u, stream, args):
     ph = hofem.Plan(2, K2, N_ORDER, X2, hofem.HOFEM_FP32_REFINED, alpha=100.0)
     uh = f.clone()
     out["heat_step_refined_ms"] = time_ms(lambda: ph.heat_steps(uh, 1, 1, stream=stream))
+    # variable coefficient a = 1 + sin(pi x) cos(3 y) / 2 at the Gauss points; PCG to 1e-10
+    pr = hofem.Plan(2, K2, N_ORDER, X2, hofem.HOFEM_FP32_REFINED)
+    x = torch.tensor(pr.quadrature_points(0), dtype=torch.float64, device="cuda")
+    aq = 1.0 + 0.5 * torch.outer(torch.sin(torch.pi * x), torch.cos(3.0 * x))
+    r = torch.empty_like(u[0])
+    out["apply_varcoef_ms"] = time_ms(lambda: pr.apply_varcoef(aq, u[0], r, stream))
+    up = torch.zeros_like(u[0])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    steps, res = pr.pcg(aq, f[0], up, tol=1e-10, maxit=200, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["pcg_to_1e-10_ms"] = e0.elapsed_time(e1)
+    out["pcg_steps"] = steps
     return out
 
 
