@@ -194,9 +194,10 @@ hofem_status hofem_mass(hofem_plan_t plan, const double* u, double* out, int nrh
  * after a first call has allocated the plan's step buffer).  Asynchronous on stream. */
 hofem_status hofem_heat_steps(hofem_plan_t plan, double* u, const double* g, int steps, int nrhs, void* stream);
 
-/* Autotuner: time every candidate launch shape (sweep lines per CTA W and DST batch J;
- * operator elements per CTA E) of this plan's solve and apply for nrhs right-hand sides
- * on its own workspace, and keep the fastest per shape in a process-wide table that
+/* Autotuner: time every candidate launch shape of this plan's solve and apply for nrhs
+ * right-hand sides (sweeps: lines per CTA W and DST batch J, from the largest J that fits
+ * down to a quarter of it; operator sweeps: elements per CTA E) on its own workspace,
+ * and keep the fastest per shape in a process-wide table that
  * later launches of any plan consult (written to / read from the file named by the
  * environment variable HOFEM_TUNE_CACHE when set).  Synchronous; reserves workspace. */
 hofem_status hofem_autotune(hofem_plan_t plan, int nrhs, void* stream);

@@ -781,19 +781,22 @@ hofem_status tune_plan(hofem_plan_s* p, int nrhs, cudaStream_t s, int* measured)
     int bw = 0, bj = 0;
     for (int W = 64; W >= 1; W >>= 1) {
       if (W > 1 && lines < W) continue;
-      int J = num_jobs_host(W, A.h.n);
-      while (J >= 1 && sweep_smem_bytes(A.h.M, A.h.n, A.h.K, W, J, tsize, strided) > kSmemLimit) --J;
-      if (J < 1) continue;
-      g_force_a = W;
-      g_force_b = J;
-      bool ok = false;
-      const double ms = time_launches(s, [&]() {
-        return run_sweep(p, w.axis, w.mode, f64, w.in, w.in_fmt, w.out, w.out_fmt, w.acc, w.acc ? p->norms : nullptr,
-                         nrhs, s);
-      }, &ok);
-      g_force_a = g_force_b = 0;
-      ++*measured;
-      if (ok && ms < best) { best = ms; bw = W; bj = J; }
+      int Jmax = num_jobs_host(W, A.h.n);
+      while (Jmax >= 1 && sweep_smem_bytes(A.h.M, A.h.n, A.h.K, W, Jmax, tsize, strided) > kSmemLimit) --Jmax;
+      if (Jmax < 1) continue;
+      // the largest DST batch, and halves of it (less shared memory, more batches)
+      for (int J = Jmax; J >= 1 && J * 4 >= Jmax; J = (J == 1 ? 0 : (J + 1) / 2)) {
+        g_force_a = W;
+        g_force_b = J;
+        bool ok = false;
+        const double ms = time_launches(s, [&]() {
+          return run_sweep(p, w.axis, w.mode, f64, w.in, w.in_fmt, w.out, w.out_fmt, w.acc,
+                           w.acc ? p->norms : nullptr, nrhs, s);
+        }, &ok);
+        g_force_a = g_force_b = 0;
+        ++*measured;
+        if (ok && ms < best) { best = ms; bw = W; bj = J; }
+      }
     }
     if (bw > 0) {
       std::lock_guard<std::mutex> lock(g_tune_mu);
