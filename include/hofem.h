@@ -121,8 +121,12 @@ typedef struct {
 
 /* Build a plan: N = 2 or 3 axes, 2 <= K[i] <= 8192 elements (any K; powers of two take
  * the fastest FFT path, other K mixed-radix passes costing the sum of K's prime factors
- * per point) and length
- * X[i] > 0 per axis, order 1 <= n <= 16, alpha > -pi^2 sum_i X_i^-2 (Sect. 2 par. 4).
+ * per point) and length X[i] > 0 per axis, order 1 <= n <= 16, alpha > -pi^2 sum_i X_i^-2
+ * (Sect. 2 par. 4).  A line of n K - 1 unknowns and one DST job must fit a CTA's shared
+ * memory at the sweeps' precision (FP64 for FP64 plans, FP32 otherwise), else
+ * HOFEM_ERR_UNSUPPORTED.  Largest K, powers of two / other K: FP32 8192 / 6081 (n = 1),
+ * 4096 / 3260 (n = 9), 2048 / 2318 (n = 16); FP64 4096 / 2879 (n = 1), 2048 / 1560
+ * (n = 9), 1024 / 1114 (n = 16).
  * Computes, on the GPU in double-double arithmetic, the 1D eigen-data of every axis:
  * for k = 1..K-1 the n eigenpairs of the theta-family of Theorem 1 part 3, for k = 0 the
  * element eigenpairs of Lemma 1 (Theorem 1 part 2).  Synchronous; allocates tables. */

@@ -963,6 +963,19 @@ hofem_status hofem_plan_orders(int N, const int* K, const int* ns, const double*
       st = HOFEM_ERR_UNSUPPORTED;
       break;
     }
+    // one line and one DST job must fit the 227 KB of shared memory of a CTA at the
+    // precision of this plan's sweeps (FP64 plans: FP64; all others: FP32)
+    const int tsize = dtype == HOFEM_FP64 ? 8 : 4;
+    if (sweep_smem_bytes(p->M[i], ns[i], K[i], 1, 1, tsize, false) > kSmemLimit) {
+      char msg[200];
+      snprintf(msg, sizeof msg,
+               "axis %d: a line of %d unknowns and its K = %d transform do not fit shared memory in %s "
+               "(smaller K, a power of two, or a lower-precision dtype)",
+               i, p->M[i], K[i], tsize == 8 ? "FP64" : "FP32");
+      g_last_error = msg;
+      st = HOFEM_ERR_UNSUPPORTED;
+      break;
+    }
   }
   if (st != HOFEM_OK) {
     for (int i = 0; i < N; ++i) free_axis(p->ax[i]);

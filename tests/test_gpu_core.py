@@ -217,3 +217,27 @@ def test_warp_fft_path_matches_oracle(monkeypatch, n, K, lines):
     plan.transform1d(0, 1, dev(y), out, lines)
     torch.cuda.synchronize()
     assert rel_l2(out.cpu().numpy(), s.inverse(y / fac, S)) <= 3e-6
+
+
+@pytest.mark.parametrize("n,K", [(1, [8192, 4]), (1, [4374, 3]), (2, [2187, 5]), (1, [6561, 3])])
+@pytest.mark.parametrize("dtype,tol", [(0, 1e-12), (1, 1e-5), (4, 1e-12)])
+def test_extreme_lengths(n, K, dtype, tol):
+    """The largest power of two (K = 8192), the most mixed-radix passes (K = 2 * 3^7: eight),
+    3^7; sizes whose line and DST job exceed shared memory at the sweeps' precision (FP64 at
+    K = 8192 and 4374; K = 3^8 = 6561 in any precision) are refused at plan time."""
+    M0 = n * K[0] - 1
+    too_big = (dtype == 0 and K[0] in (8192, 4374)) or K[0] == 6561
+    if too_big:
+        with pytest.raises(H().HofemError) as e:
+            H().Plan(2, K, n, [1.0, 0.5], dtype)
+        assert e.value.status == 2 and "shared memory" in str(e.value)
+        return
+    plan = H().Plan(2, K, n, [1.0, 0.5], dtype)
+    Ms = [M0, n * K[1] - 1]
+    f = np.random.default_rng(K[0]).standard_normal([1] + Ms)
+    ref = osolve.solve_tensor(f, [n, n], K, [1.0, 0.5])
+    fd = dev(f)
+    ud = torch.zeros_like(fd)
+    plan.solve(fd, ud, 1)
+    torch.cuda.synchronize()
+    assert rel_l2(ud.cpu().numpy(), ref) <= tol
