@@ -615,7 +615,7 @@ hofem_status banded_once(hofem_plan_s* p, const double* f, double* u, int nrhs, 
 hofem_status varcoef_apply(hofem_plan_s* p, const double* aq, const double* u, double* r, cudaStream_t s) {
   if (p->N != 2 || p->ax[0].h.n != p->ax[1].h.n || p->ax[0].h.n > 9)
     return fail(HOFEM_ERR_UNSUPPORTED, "the variable-coefficient operator is 2D with one order n <= 9");
-  const int n = p->ax[0].h.n, G = n + 1;
+  const int n = p->ax[0].h.n;
   if (!p->vcB) {
     std::vector<double> B, D, w;
     element_basis_tables(n, &B, &D, &w);
@@ -639,7 +639,6 @@ hofem_status varcoef_apply(hofem_plan_s* p, const double* aq, const double* u, d
   V.n = n;
   V.s0 = 4.0 * (double)p->K[0] * (double)p->K[0] / (p->X[0] * p->X[0]);
   V.s1 = 4.0 * (double)p->K[1] * (double)p->K[1] / (p->X[1] * p->X[1]);
-  (void)G;
   HOFEM_CUDA(cudaMemsetAsync(r, 0, (size_t)p->total * sizeof(double), s), "memset (varcoef)");
   HOFEM_CUDA(launch_varcoef(V, s), "varcoef launch");
   p->info.kernel_launches += 1;
