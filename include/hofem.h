@@ -265,8 +265,8 @@ hofem_status hofem_profile(hofem_plan_t plan, int enable);
 hofem_status hofem_get_profile(hofem_plan_t plan, hofem_kernel_time* out, int max_entries, int* count);
 void hofem_destroy(hofem_plan_t plan);
 
-/* Batched solves of independent problems of uneven K, n, X and nrhs (a batch scheduler): one plan per problem with its workspace reserved up front.  The
- * first hofem_batch_solve captures every problem's solve (the refined dtypes with their
+/* Batched solves of independent problems of uneven K, n, X and nrhs: one plan per problem
+ * with its workspace reserved up front.  The first hofem_batch_solve captures every problem's solve (the refined dtypes with their
  * fixed step count) into one CUDA graph whose branches spread the problems over up to 16
  * streams, so independent problems run concurrently; later calls with the same pointer
  * arrays relaunch that graph (other pointers recapture it).  Synchronous plan; errors of
