@@ -266,11 +266,12 @@ hofem_status hofem_get_profile(hofem_plan_t plan, hofem_kernel_time* out, int ma
 void hofem_destroy(hofem_plan_t plan);
 
 /* Batched solves of independent problems of uneven K, n, X and nrhs: one plan per problem
- * with its workspace reserved up front.  The first hofem_batch_solve captures every problem's solve (the refined dtypes with their
- * fixed step count) into one CUDA graph whose branches spread the problems over up to 16
- * streams, so independent problems run concurrently; later calls with the same pointer
- * arrays relaunch that graph (other pointers recapture it).  Synchronous plan; errors of
- * one problem name its index in hofem_last_error. */
+ * with its workspace reserved up front.  The first hofem_batch_solve captures every
+ * problem's solve (the refined dtypes with their fixed step count) into one CUDA graph
+ * whose branches spread the problems over up to 16 streams, so independent problems run
+ * concurrently; later calls with the same pointer arrays relaunch that graph (other
+ * pointers recapture it).  Synchronous plan; errors of one problem name its index in
+ * hofem_last_error. */
 hofem_status hofem_batch_plan(int count, const hofem_problem* probs, int dtype, hofem_batch_t* out);
 
 /* hofem_autotune for every problem (shapes shared between problems are measured once). */
