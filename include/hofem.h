@@ -140,8 +140,9 @@ hofem_status hofem_plan_orders(int N, const int* K, const int* n, const double* 
                                hofem_plan_t* out);
 
 /* Refined dtypes only: iters = residual/correction steps after the first low-precision
- * solve (0..100; default FP32 2 when every K is a power of two, else 3; BF16 and FP16 8); tol > 0 additionally stops early once ||delta||/||u|| <= tol,
- * which synchronises the stream once per step.  tol = 0 keeps a fixed count (capturable). */
+ * solve (0..100; default FP32 2 when every K is a power of two, else 3; BF16 and FP16 8);
+ * tol > 0 additionally stops early once ||delta||/||u|| <= tol, which synchronises the
+ * stream once per step.  tol = 0 keeps a fixed count (capturable). */
 hofem_status hofem_set_refinement(hofem_plan_t plan, int iters, double tol);
 
 /* The (n+1)-point Gauss-Legendre quadrature points of the load vector along `axis`
