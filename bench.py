@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the plan-time autotuner (built-in launch shapes)")
+    ap.add_argument("--batch", action="store_true",
+                    help="also time the batched form: 512 uneven 2D problems in one graph launch, refined vs FP64")
     ap.add_argument("--extras", action="store_true",
                     help="also time on-device f^h, algorithm (b) and a heat step at the same size")
     ap.add_argument("--elements", type=int, default=K_ELEM,
@@ -211,6 +213,42 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batch_paths(hofem, torch, stream, steps=3):
+    """The batched form: 512 independent 2D problems (K 32..512 and n 2..8 log-uniform, X per
+    axis in [0.5, 4], 1-8 RHS each) solved by one CUDA-graph launch per step, FP32 + FP64
+    refinement against the FP64 batch; unknown-RHS per second (the plan is outside the time)."""
+    from paper_1609_07758_gb300 import inputs
+    probs = inputs.batch_problems(4)
+    gen = torch.Generator(device="cuda").manual_seed(4)
+    fs = [torch.randn((q["nrhs"],) + tuple(q["n"] * k - 1 for k in q["K"]), dtype=torch.float64, device="cuda",
+                      generator=gen) for q in probs]
+    out = {"problems": len(probs)}
+
+    def run(dtype):
+        b = hofem.Batch(probs, dtype)
+        us = [torch.empty_like(x) for x in fs]
+        b.solve(fs, us, stream)                        # capture + first launch
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            b.solve(fs, us, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        info = b.info()
+        b.close()
+        return e0.elapsed_time(e1) / steps, us, info
+
+    ms_r, ur, info = run(hofem.HOFEM_FP32_REFINED)
+    ms_d, ud, _ = run(hofem.HOFEM_FP64)
+    worst = max(float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c)) for a, c in zip(ur, ud))
+    out.update({"unknown_rhs": info.unknowns, "graph_nodes": info.graph_nodes,
+                "refined_ms": ms_r, "refined_unknowns_per_s": info.unknowns / (ms_r / 1e3),
+                "fp64_ms": ms_d, "fp64_unknowns_per_s": info.unknowns / (ms_d / 1e3),
+                "speedup_refined_vs_fp64": ms_d / ms_r, "max_rel_l2_refined_vs_fp64": worst})
+    return out
+
+
 def extra_paths(hofem, torch, f, u, stream, args):
     """ms per call of the widened paths at the benchmark size (CUDA events, after warm-up)."""
     K2, X2 = [K_ELEM, K_ELEM], [X_LEN, X_LEN]
@@ -356,6 +394,7 @@ def main():
     extras = None
     if args.extras:
         extras = extra_paths(hofem, torch, f, u, stream, args)
+    batched = batch_paths(hofem, torch, stream) if args.batch else None
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -408,6 +447,7 @@ def main():
                                          "h2d_bytes_per_step": 8 * UNKNOWNS, "d2h_bytes_per_step": 8 * UNKNOWNS},
         "gpu_launches": launches,
         **({"extras_ms": extras} if extras else {}),
+        **({"batched": batched} if batched else {}),
         "clocks": clock_info,
     }
     if rank == 0:
