@@ -85,6 +85,11 @@ typedef struct {
   long long kernel_launches; /* kernels this plan has launched since it was created */
   long long tuned_shapes;   /* launch-shape candidates measured by hofem_autotune */
   int orders[3];            /* element order per axis (n above is their maximum) */
+  int fft_len[3];           /* per axis, the length of the FFTs its DSTs run at the plan's sweep
+                               precision: K for a power of two or direct mixed-radix passes
+                               over the prime factors of K, else the power-of-two length of
+                               the Bluestein (chirp-z) convolution chosen for K with large
+                               prime factors */
 } hofem_info;
 
 /* One problem of a batch: N = 2 or 3 axes with K[i] elements of length X[i] (entries

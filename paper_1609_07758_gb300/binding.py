@@ -43,7 +43,7 @@ class hofem_info(ctypes.Structure):
         ("table_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
         ("lines_per_cta", ctypes.c_int * 3), ("threads_per_cta", ctypes.c_int),
         ("kernel_launches", ctypes.c_longlong), ("tuned_shapes", ctypes.c_longlong),
-        ("orders", ctypes.c_int * 3),
+        ("orders", ctypes.c_int * 3), ("fft_len", ctypes.c_int * 3),
     ]
 
 

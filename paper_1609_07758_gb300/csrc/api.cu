@@ -52,6 +52,7 @@ struct DevAxis {
   double *lam64 = nullptr, *mix64 = nullptr, *evec64 = nullptr, *tw64 = nullptr;
   float *lam32 = nullptr, *mix32 = nullptr, *evec32 = nullptr, *tw32 = nullptr;
   int npass = 0, radix[8] = {0};
+  int nb = 0;                    // Bluestein length of the K-point DFTs (0: direct passes)
   int mixNP = 0;
 };
 
@@ -240,13 +241,13 @@ int num_jobs_host(int W, int n) { return W * ((n - 1) / 2) + (((n & 1) == 0) ? W
 // Lines per CTA (W, power of two) and DST jobs per batch (J) for one sweep: the fewest
 // DST batches (block-wide barrier rounds) per line, then the largest W (more reuse of
 // each mixing-table row), keeping >= 2 CTAs per SM when there are enough lines.
-bool choose_sweep(int M, int n, int K, int tsize, long long lines, bool strided, int* W_out, int* J_out) {
+bool choose_sweep(int M, int n, int K, int NB, int tsize, long long lines, bool strided, int* W_out, int* J_out) {
   (void)strided;
   // tuning override "W:J" (both must fit; used to explore launch shapes)
   if (const char* env = getenv("HOFEM_SWEEP_CFG")) {
     int W = 0, J = 0;
     if (sscanf(env, "%d:%d", &W, &J) == 2 && W >= 1 && (W & (W - 1)) == 0 && J >= 1 &&
-        J <= num_jobs_host(W, n) && sweep_smem_bytes(M, n, K, W, J, tsize, strided) <= kSmemLimit) {
+        J <= num_jobs_host(W, n) && sweep_smem_bytes(M, n, K, NB, W, J, tsize, strided) <= kSmemLimit) {
       *W_out = W;
       *J_out = J;
       return true;
@@ -258,7 +259,7 @@ bool choose_sweep(int M, int n, int K, int tsize, long long lines, bool strided,
     if (W > 1 && lines / W < 2 * kSMs) continue;
     const int jobs = num_jobs_host(W, n);
     int J = jobs;
-    while (J >= 1 && sweep_smem_bytes(M, n, K, W, J, tsize, strided) > kSmemLimit) --J;
+    while (J >= 1 && sweep_smem_bytes(M, n, K, NB, W, J, tsize, strided) > kSmemLimit) --J;
     if (J < 1) continue;
     const int batches = (jobs + J - 1) / J;
     const double score = (double)batches / W;
@@ -337,11 +338,19 @@ bool tuned_lookup(const TuneKey& k, int* a, int* b) {
   return true;
 }
 
+// Bluestein length a sweep of this axis uses at work-precision size tsize: the plan's
+// choice when one line and one job of it fit shared memory, else the direct passes.
+int sweep_nb(const DevAxis& A, int tsize) {
+  if (A.nb > 0 && sweep_smem_bytes(A.h.M, A.h.n, A.h.K, A.nb, 1, 1, tsize, false) <= kSmemLimit) return A.nb;
+  return 0;
+}
+
 TuneKey sweep_key(const hofem_plan_s* p, int axis, int mode, bool f64, long long nrhs, long long lines_override) {
   const DevAxis& A = p->ax[axis];
   Geo g = geometry(p, axis);
   if (lines_override >= 0) g = Geo{lines_override, 1};
-  return TuneKey{0, A.h.M, A.h.n, A.h.K, f64 ? 8 : 4, g.inner > 1 ? 1 : 0, mode, nrhs * g.outer_per_rhs * g.inner};
+  const int kind = sweep_nb(A, f64 ? 8 : 4) > 0 ? 2 : 0;   // 2: Bluestein sweeps
+  return TuneKey{kind, A.h.M, A.h.n, A.h.K, f64 ? 8 : 4, g.inner > 1 ? 1 : 0, mode, nrhs * g.outer_per_rhs * g.inner};
 }
 
 TuneKey apply_key(const hofem_plan_s* p, int axis, int mode, long long nrhs) {
@@ -368,11 +377,14 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   const bool wfft = !f64 && is_pow2(A.h.K) && A.h.K >= 32 && A.h.K <= 1024 && wf_env && wf_env[0] == '1' &&
                     choose_sweep_wfft(A.h.M, A.h.n, A.h.K, lines, &W, &nwarps);
   const TuneKey key = sweep_key(p, axis, mode, f64, nrhs, lines_override);
+  const int NB = sweep_nb(A, tsize);
   if (wfft) {
   } else if (g_force_a > 0) {
     W = g_force_a;
     J = g_force_b;
-  } else if (!tuned_lookup(key, &W, &J) && !choose_sweep(A.h.M, A.h.n, A.h.K, tsize, lines, strided, &W, &J)) {
+  } else if (!(tuned_lookup(key, &W, &J) &&
+               sweep_smem_bytes(A.h.M, A.h.n, A.h.K, NB, W, J, tsize, strided) <= kSmemLimit) &&
+             !choose_sweep(A.h.M, A.h.n, A.h.K, NB, tsize, lines, strided, &W, &J)) {
     return fail(HOFEM_ERR_UNSUPPORTED, "no launch configuration fits shared memory for this axis");
   }
   P.outer = nrhs * g.outer_per_rhs;
@@ -430,10 +442,19 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
     P.radix[i] = A.radix[i];
     P.radix_log[i] = A.radix[i] > 0 ? 31 - __builtin_clz(A.radix[i]) : 0;
   }
+  P.nb = wfft ? 0 : NB;
+  P.nb_log = P.nb_npass = 0;
+  for (int i = 0; i < 4; ++i) P.nb_radix[i] = 0;
+  if (P.nb > 0) {
+    int rb[8] = {0};
+    radix_plan(P.nb, &P.nb_npass, rb);
+    for (int i = 0; i < P.nb_npass && i < 4; ++i) P.nb_radix[i] = rb[i];
+    P.nb_log = 31 - __builtin_clz(P.nb);
+  }
   P.jobs_per_batch = J;
   P.wfft = wfft ? 1 : 0;
   P.wf_xs = wfft ? wfft_row_stride(A.h.K) : 0;
-  P.fbuf_complex = wfft ? wfft_fbuf_complex(W, A.h.n, A.h.K, nwarps) : sweep_fbuf_complex(A.h.K, J, tsize);
+  P.fbuf_complex = wfft ? wfft_fbuf_complex(W, A.h.n, A.h.K, nwarps) : sweep_fbuf_complex(A.h.K, P.nb, J, tsize);
   if (strided) { P.ps = W; P.ws = 1; } else { P.ps = 1; P.ws = A.h.M; }
   P.tile_elems = sweep_tile_elems(A.h.M, W, tsize);
   P.threads = wfft ? 32 * nwarps : (f64 ? 512 : HOFEM_F32_THREADS);
@@ -781,7 +802,9 @@ hofem_status tune_plan(hofem_plan_s* p, int nrhs, cudaStream_t s, int* measured)
     for (int W = 64; W >= 1; W >>= 1) {
       if (W > 1 && lines < W) continue;
       int Jmax = num_jobs_host(W, A.h.n);
-      while (Jmax >= 1 && sweep_smem_bytes(A.h.M, A.h.n, A.h.K, W, Jmax, tsize, strided) > kSmemLimit) --Jmax;
+      while (Jmax >= 1 && sweep_smem_bytes(A.h.M, A.h.n, A.h.K, sweep_nb(A, tsize), W, Jmax, tsize, strided) >
+                              kSmemLimit)
+        --Jmax;
       if (Jmax < 1) continue;
       // the largest DST batch, and halves of it (less shared memory, more batches)
       for (int J = Jmax; J >= 1 && J * 4 >= Jmax; J = (J == 1 ? 0 : (J + 1) / 2)) {
@@ -934,11 +957,23 @@ hofem_status hofem_plan_orders(int N, const int* K, const int* ns, const double*
     int same = -1;
     for (int j = 0; j < i; ++j)
       if (K[j] == K[i] && X[j] == X[i] && ns[j] == ns[i]) same = j;
-    if (same >= 0) {
+    // Bluestein form of the DFTs for K with large prime factors (HOFEM_FFT=direct or
+    // =bluestein overrides the cost model for every non-power-of-two K)
+    a.nb = bluestein_len(K[i]);
+    if (const char* fe = getenv("HOFEM_FFT")) {
+      if (!strcmp(fe, "direct")) a.nb = 0;
+      if (!strcmp(fe, "bluestein") && !is_pow2(K[i])) a.nb = bluestein_pow2(K[i]);
+    }
+    if (same >= 0 && p->ax[same].nb == a.nb) {
       a.h = p->ax[same].h;
     } else {
       st = build_axis_tables(ns[i], K[i], X[i], &a.h, &err);
       if (st != HOFEM_OK) { g_last_error = err; break; }
+      if (a.nb > 0) {
+        int np = 0, rb[8] = {0};
+        radix_plan(a.nb, &np, rb);
+        bluestein_tables(K[i], a.nb, np, rb, &a.h.tw);
+      }
     }
     size_t& tb = p->table_bytes;
     if ((st = upload(a.h.lam, &a.lam64, &tb)) != HOFEM_OK) break;
@@ -965,7 +1000,7 @@ hofem_status hofem_plan_orders(int N, const int* K, const int* ns, const double*
     // one line and one DST job must fit the 227 KB of shared memory of a CTA at the
     // precision of this plan's sweeps (FP64 plans: FP64; all others: FP32)
     const int tsize = dtype == HOFEM_FP64 ? 8 : 4;
-    if (sweep_smem_bytes(p->M[i], ns[i], K[i], 1, 1, tsize, false) > kSmemLimit) {
+    if (sweep_smem_bytes(p->M[i], ns[i], K[i], sweep_nb(a, tsize), 1, 1, tsize, false) > kSmemLimit) {
       char msg[200];
       snprintf(msg, sizeof msg,
                "axis %d: a line of %d unknowns and its K = %d transform do not fit shared memory in %s "
@@ -995,6 +1030,10 @@ hofem_status hofem_plan_orders(int N, const int* K, const int* ns, const double*
   inf.N = N;
   inf.n = n;
   for (int i = 0; i < N; ++i) inf.orders[i] = ns[i];
+  for (int i = 0; i < N; ++i) {
+    const int nb = sweep_nb(p->ax[i], dtype == HOFEM_FP64 ? 8 : 4);
+    inf.fft_len[i] = nb > 0 ? nb : K[i];
+  }
   for (int i = 0; i < N; ++i) {
     inf.K[i] = K[i];
     inf.M[i] = p->M[i];

@@ -40,6 +40,14 @@ struct AxisTables {
 
 hofem_status build_axis_tables(int n, int K, double X, AxisTables* out, std::string* err);
 
+// Appends to tw (2K complex DST twiddles, interleaved re/im) the tables of the Bluestein
+// form of the K-point DFT (outputs m < H = (K - 1) / 2 + 1) with convolution length NB (a
+// power of two >= K - 1 + H) whose NB-point FFTs run the DIF passes of radices
+// radix[0..npass): exp(-i pi t / NB) for t < 2 NB; the chirp c_j = exp(-i pi j^2 / K) for
+// j < K; the DFT of the filter b_d = conj(c_|d|) (lags -(K-1) <= d < H, indices mod NB),
+// divided by NB, at the passes' output slots.
+void bluestein_tables(int K, int NB, int npass, const int* radix, std::vector<double>* tw);
+
 // (n+1)-point Gauss-Legendre nodes xi (ascending) and T[a (n+1) + g] = w_g e_a(xi_g).
 void element_load_table(int n, std::vector<double>* T, std::vector<double>* xi);
 // B[g][a] = e_a(xi_g), D[g][a] = e_a'(xi_g) and the weights w_g of that rule.

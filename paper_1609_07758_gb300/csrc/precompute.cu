@@ -17,6 +17,7 @@
 // C~ e . e = 1 (Theorem 1 part 2), norm K.  Both are solved by Cholesky of the mass
 // matrix and cyclic Jacobi on L^{-1} A L^{-T}, all in double-double.
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -584,6 +585,64 @@ cleanup:
   cudaFree(d_status);
 #undef PC_CHECK
   return st;
+}
+
+void bluestein_tables(int K, int NB, int npass, const int* radix, std::vector<double>* tw) {
+  using cd = std::complex<double>;
+  std::vector<double> wB(4 * (size_t)NB);
+  for (int t = 0; t < 2 * NB; ++t) {
+    dd sn, cs;
+    dd_sincos_pi_frac(t, NB, &sn, &cs);
+    wB[2 * t] = dd_to_double(cs);
+    wB[2 * t + 1] = -dd_to_double(sn);
+  }
+  // chirp: j^2 reduced mod 2K indexes the 2K-th roots already in tw
+  std::vector<double> ch(2 * (size_t)K);
+  std::vector<cd> b(NB, cd(0.0, 0.0));
+  for (int j = 0; j < K; ++j) {
+    const long long r = ((long long)j * j) % (2LL * K);
+    ch[2 * j] = (*tw)[2 * r];
+    ch[2 * j + 1] = (*tw)[2 * r + 1];
+    const cd cc(ch[2 * j], -ch[2 * j + 1]);
+    if (j <= (K - 1) / 2) b[j] = cc;           // lags 0 .. H-1 (the outputs used)
+    if (j > 0) b[NB - j] = cc;                  // lags -(K-1) .. -1
+  }
+  // B = DFT_NB(b): radix-2, natural order (bit-reversal permutation, then butterflies)
+  int lg = 0;
+  while ((1 << lg) < NB) ++lg;
+  for (int i = 0; i < NB; ++i) {
+    int r = 0;
+    for (int k = 0; k < lg; ++k) r |= ((i >> k) & 1) << (lg - 1 - k);
+    if (r > i) std::swap(b[i], b[r]);
+  }
+  for (int len = 2; len <= NB; len <<= 1) {
+    const int step = 2 * NB / len;            // exp(-2 pi i j / len) = wB[j step]
+    for (int s0 = 0; s0 < NB; s0 += len)
+      for (int j = 0; j < len / 2; ++j) {
+        const cd w(wB[2 * (size_t)j * step], wB[2 * (size_t)j * step + 1]);
+        const cd u = b[s0 + j], v = b[s0 + j + len / 2] * w;
+        b[s0 + j] = u + v;
+        b[s0 + j + len / 2] = u - v;
+      }
+  }
+  // output slot of frequency k after the DIF passes: the low digit of k selects the top
+  // digit of the slot
+  std::vector<double> filt(2 * (size_t)NB);
+  for (int k = 0; k < NB; ++k) {
+    int slot = 0, sh = lg, m = k;
+    for (int ps = 0; ps < npass; ++ps) {
+      int lb = 0;
+      while ((1 << lb) < radix[ps]) ++lb;
+      sh -= lb;
+      slot |= (m & (radix[ps] - 1)) << sh;
+      m >>= lb;
+    }
+    filt[2 * slot] = b[k].real() / NB;
+    filt[2 * slot + 1] = b[k].imag() / NB;
+  }
+  tw->insert(tw->end(), wB.begin(), wB.end());
+  tw->insert(tw->end(), ch.begin(), ch.end());
+  tw->insert(tw->end(), filt.begin(), filt.end());
 }
 
 }  // namespace hofem

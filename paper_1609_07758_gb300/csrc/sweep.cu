@@ -181,18 +181,94 @@ __device__ __noinline__ void fft_pass(typename Cx<T>::type* buf, int logN, int n
   __syncthreads();
 }
 
-template <typename T>
+// The inverse of one fft_pass up to the factor R, on conjugates: with conj(y) in the
+// pass's output slots, z_q = w_L^{jq} conj(y)_{j + qL/R} and the forward R-point DFT of z
+// give R conj(x_r) in the input slots j + r L/R.  Run over the passes of a DIF network in
+// reverse order, this maps conj(Y) in digit-reversed order to N conj(IDFT(Y)) in natural
+// order.
+template <typename T, int R>
+__device__ __noinline__ void fft_pass_inv(typename Cx<T>::type* buf, int logN, int nfft, int logL,
+                                          const typename Cx<T>::type* __restrict__ tw) {
+  using C = typename Cx<T>::type;
+  constexpr int LR = Log2<R>::v;
+  const int N = 1 << logN;
+  const int logQ = logL - LR;
+  const int logB = logN - LR;
+  const int nb = nfft << logB;
+  const int FS = fft_stride<T>(N);
+  const int tsh = logN - logL + 1;
+  const int mask2N = 2 * N - 1;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const int f = b >> logB;
+    const int rem = b & ((1 << logB) - 1);
+    const int blk = rem >> logQ;
+    const int j = rem & ((1 << logQ) - 1);
+    C* base = buf + (size_t)f * FS;
+    const int e0 = (blk << logL) + j;
+    C v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = base[fpad<T>(e0 + (q << logQ))];
+    if (j != 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) v[q] = c_mul(v[q], tw[((j * q) << tsh) & mask2N]);
+    }
+    dft_reg<T, R>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) base[fpad<T>(e0 + (r << logQ))] = v[r];
+  }
+  __syncthreads();
+}
+
+// DIF passes over nfft FFTs of length 2^logN: the K plan (P.radix) or, NBPLAN, the
+// Bluestein length's plan (P.nb_radix); INV runs the inverse network (fft_pass_inv, passes
+// in reverse order).
+template <typename T, bool NBPLAN = false, bool INV = false>
 __device__ void fft_all(typename Cx<T>::type* buf, int logN, int nfft, const SweepParams& P,
                         const typename Cx<T>::type* __restrict__ tw) {
-  int logL = logN;
-  for (int ps = 0; ps < P.npass; ++ps) {
-    const int R = P.radix[ps];
-    if (R == 16) fft_pass<T, 16>(buf, logN, nfft, logL, tw);
-    else if (R == 8) fft_pass<T, 8>(buf, logN, nfft, logL, tw);
-    else if (R == 4) fft_pass<T, 4>(buf, logN, nfft, logL, tw);
-    else fft_pass<T, 2>(buf, logN, nfft, logL, tw);
-    logL -= (R == 16) ? 4 : (R == 8) ? 3 : (R == 4) ? 2 : 1;
+  auto lg = [](int R) { return (R == 16) ? 4 : (R == 8) ? 3 : (R == 4) ? 2 : 1; };
+  const int np = NBPLAN ? P.nb_npass : P.npass;
+  if constexpr (!INV) {
+    int logL = logN;
+    for (int ps = 0; ps < np; ++ps) {
+      const int R = NBPLAN ? P.nb_radix[ps] : P.radix[ps];
+      if (R == 16) fft_pass<T, 16>(buf, logN, nfft, logL, tw);
+      else if (R == 8) fft_pass<T, 8>(buf, logN, nfft, logL, tw);
+      else if (R == 4) fft_pass<T, 4>(buf, logN, nfft, logL, tw);
+      else fft_pass<T, 2>(buf, logN, nfft, logL, tw);
+      logL -= lg(R);
+    }
+  } else {
+    int logL = logN;                            // block length of the last pass
+    for (int ps = 0; ps + 1 < np; ++ps) logL -= lg((NBPLAN ? P.nb_radix[ps] : P.radix[ps]));
+    for (int ps = np - 1; ps >= 0; --ps) {
+      const int R = (NBPLAN ? P.nb_radix[ps] : P.radix[ps]);
+      if (R == 16) fft_pass_inv<T, 16>(buf, logN, nfft, logL, tw);
+      else if (R == 8) fft_pass_inv<T, 8>(buf, logN, nfft, logL, tw);
+      else if (R == 4) fft_pass_inv<T, 4>(buf, logN, nfft, logL, tw);
+      else fft_pass_inv<T, 2>(buf, logN, nfft, logL, tw);
+      if (ps > 0) logL += lg((NBPLAN ? P.nb_radix[ps - 1] : P.radix[ps - 1]));
+    }
   }
+}
+
+// Bluestein convolution of nfft chirped sequences (stored, zero-padded to nb, by
+// dst_load_general): forward DIF FFT, product with the filter's transform (already / nb),
+// conjugated, then the inverse network; leaves conj((x c) * conj(c)) in natural order.
+template <typename T>
+__device__ void bluestein_conv(typename Cx<T>::type* buf, int nfft, const SweepParams& P,
+                               const typename Cx<T>::type* __restrict__ twB,
+                               const typename Cx<T>::type* __restrict__ filt) {
+  using C = typename Cx<T>::type;
+  fft_all<T, true, false>(buf, P.nb_log, nfft, P, twB);
+  const int FS = fft_stride<T>(P.nb), items = nfft << P.nb_log, mask = P.nb - 1;
+  for (int i = threadIdx.x; i < items; i += blockDim.x) {
+    const int f = i >> P.nb_log, s = i & mask;
+    C* e = buf + (size_t)f * FS + fpad<T>(s);
+    const C y = c_mul(*e, filt[s]);
+    *e = C{y.x, -y.y};
+  }
+  __syncthreads();
+  fft_all<T, true, true>(buf, P.nb_log, nfft, P, twB);
 }
 
 // Memory slot of frequency m after the DIF passes: the low digit of m (base R_1) selects
@@ -369,14 +445,18 @@ __device__ __forceinline__ void dst_out(const typename Cx<T>::type* buf, int jb,
 }
 
 // dst_load for any K: t = 0 .. K/2 fills slots t and K - t of u and v.
+// With a Bluestein plan (chirp non-null) every entry t is stored times c_t, the FFTs have
+// length (and stride) of P.nb, and entries K .. nb-1 are zeroed.
 template <typename T>
 __device__ __noinline__ void dst_load_general(const Tile<T> tl, typename Cx<T>::type* buf, int j0, int nj, int W,
-                                              int n, int K, bool inverse, const typename Cx<T>::type* __restrict__ tw) {
+                                              int n, int K, bool inverse, const typename Cx<T>::type* __restrict__ tw,
+                                              const typename Cx<T>::type* __restrict__ chirp, int NB) {
   using C = typename Cx<T>::type;
   const int per = K / 2 + 1;
   const int logW = 31 - __clz(W);
   const int items = nj * per;
-  const int FS = fft_stride<T>(K);
+  const int FS = fft_stride<T>(chirp ? NB : K);
+  auto ch = [&](C v, int t) { return chirp ? c_mul(v, chirp[t]) : v; };
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
     const int jb = it / per, t = it - jb * per;
     const Job job = job_of(j0 + jb, W, logW, n);
@@ -390,25 +470,44 @@ __device__ __noinline__ void dst_load_general(const Tile<T> tl, typename Cx<T>::
     const C x1 = pair_x(tl, job, t, n, K, inverse);
     if (2 * t == K) {                           // u = 0, v = 2 x w^{K/2}
       U[fpad<T>(t)] = C{(T)0, (T)0};
-      V[fpad<T>(t)] = c_mul(c_add(x1, x1), tw[t]);
+      V[fpad<T>(t)] = ch(c_mul(c_add(x1, x1), tw[t]), t);
       continue;
     }
     const C x2 = pair_x(tl, job, K - t, n, K, inverse);
     const C d = c_sub(x1, x2), sm = c_add(x1, x2);
-    U[fpad<T>(t)] = d;
-    U[fpad<T>(K - t)] = C{-d.x, -d.y};
-    V[fpad<T>(t)] = c_mul(sm, tw[t]);
-    V[fpad<T>(K - t)] = c_mul(sm, tw[K - t]);
+    U[fpad<T>(t)] = ch(d, t);
+    U[fpad<T>(K - t)] = ch(C{-d.x, -d.y}, K - t);
+    V[fpad<T>(t)] = ch(c_mul(sm, tw[t]), t);
+    V[fpad<T>(K - t)] = ch(c_mul(sm, tw[K - t]), K - t);
+  }
+  if (chirp) {
+    const int pad = NB - K, tail = 2 * nj * pad;
+    for (int it = threadIdx.x; it < tail; it += blockDim.x) {
+      const int f = it / pad, t = K + (it - f * pad);
+      buf[(size_t)f * FS + fpad<T>(t)] = C{(T)0, (T)0};
+    }
   }
 }
 
+// DST output k of job jb from the FFT results (u at even k, v at odd k): after the direct
+// passes in their digit order, after a Bluestein convolution at m = k / 2 in natural order
+// as X_m = c_m conj(buf[m]).
 template <typename T>
 __device__ __forceinline__ void dst_out_general(const typename Cx<T>::type* buf, int jb, int K, int k, T* a, T* b,
-                                                const SweepParams& P) {
-  const int FS = fft_stride<T>(K);
-  const typename Cx<T>::type* U = buf + (size_t)(2 * jb) * FS;
-  const int pos = fpad<T>(fft_pos_general(k >> 1, P));
-  const typename Cx<T>::type R = (k & 1) ? U[FS + pos] : U[pos];
+                                                const SweepParams& P, const typename Cx<T>::type* __restrict__ chirp) {
+  using C = typename Cx<T>::type;
+  const int m = k >> 1;
+  C R;
+  if (chirp) {
+    const int FS = fft_stride<T>(P.nb);
+    const C y = buf[(size_t)(2 * jb + (k & 1)) * FS + fpad<T>(m)];
+    R = c_mul(C{y.x, -y.y}, chirp[m]);
+  } else {
+    const int FS = fft_stride<T>(K);
+    const C* U = buf + (size_t)(2 * jb) * FS;
+    const int pos = fpad<T>(fft_pos_general(m, P));
+    R = (k & 1) ? U[FS + pos] : U[pos];
+  }
   *a = -R.y;
   *b = R.x;
 }
@@ -599,17 +698,19 @@ __device__ void forward_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
         if (job.mb >= 0) tl.at((k - 1) * n + slot_of(job.mb, n), job.wb) = b;
       }
     } else {
-      dst_load_general<T>(tl, fbuf, j0, nj, W, n, K, false, tw);
+      const typename Cx<T>::type* chirp = P.nb ? tw + 2 * K + 2 * P.nb : nullptr;
+      dst_load_general<T>(tl, fbuf, j0, nj, W, n, K, false, tw, chirp, P.nb);
       __syncthreads();
-      const typename Cx<T>::type* res =
-          fft_all_general<T>(fbuf, fbuf + (size_t)J * 2 * fft_stride<T>(K), K, 2 * nj, P, tw);
+      const typename Cx<T>::type* res = fbuf;
+      if (P.nb) bluestein_conv<T>(fbuf, 2 * nj, P, tw + 2 * K, chirp + K);
+      else res = fft_all_general<T>(fbuf, fbuf + (size_t)J * 2 * fft_stride<T>(K), K, 2 * nj, P, tw);
       const int items = nj * K;
       for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int jb = it / K, k = it - jb * K;
         if (k == 0) continue;
         const Job job = job_of(j0 + jb, W, logW, n);
         T a, b;
-        dst_out_general<T>(res, jb, K, k, &a, &b, P);
+        dst_out_general<T>(res, jb, K, k, &a, &b, P, chirp);
         tl.at((k - 1) * n + slot_of(job.ma, n), job.wa) = a;
         if (job.mb >= 0) tl.at((k - 1) * n + slot_of(job.mb, n), job.wb) = b;
       }
@@ -642,14 +743,16 @@ __device__ void inverse_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
   for (int j0 = 0; j0 < nj_tot; j0 += J) {
     const int nj = min(J, nj_tot - j0);
     const typename Cx<T>::type* res = fbuf;
+    const typename Cx<T>::type* chirp = (GK && P.nb) ? tw + 2 * K + 2 * P.nb : nullptr;
     if constexpr (!GK) {
       dst_load<T>(tl, fbuf, j0, nj, W, n, K, true, tw);
       __syncthreads();
       fft_all<T>(fbuf, logK, 2 * nj, P, tw);
     } else {
-      dst_load_general<T>(tl, fbuf, j0, nj, W, n, K, true, tw);
+      dst_load_general<T>(tl, fbuf, j0, nj, W, n, K, true, tw, chirp, P.nb);
       __syncthreads();
-      res = fft_all_general<T>(fbuf, fbuf + (size_t)J * 2 * fft_stride<T>(K), K, 2 * nj, P, tw);
+      if (P.nb) bluestein_conv<T>(fbuf, 2 * nj, P, tw + 2 * K, chirp + K);
+      else res = fft_all_general<T>(fbuf, fbuf + (size_t)J * 2 * fft_stride<T>(K), K, 2 * nj, P, tw);
     }
     // post-combine into physical rows
     const int items = nj * K;
@@ -668,8 +771,8 @@ __device__ void inverse_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
         if (j - 1 >= 1) dst_out<T>(res, jb, K, logK, j - 1, &a0, &b0, P);
         if (j <= K - 1) dst_out<T>(res, jb, K, logK, j, &a1, &b1, P);
       } else {
-        if (j - 1 >= 1) dst_out_general<T>(res, jb, K, j - 1, &a0, &b0, P);
-        if (j <= K - 1) dst_out_general<T>(res, jb, K, j, &a1, &b1, P);
+        if (j - 1 >= 1) dst_out_general<T>(res, jb, K, j - 1, &a0, &b0, P, chirp);
+        if (j <= K - 1) dst_out_general<T>(res, jb, K, j, &a1, &b1, P, chirp);
       }
       if (job.ma == 0) {                        // nodes of line wa (and maybe wb)
         if (j <= K - 1) {
@@ -1132,10 +1235,37 @@ int sweep_tile_elems(int M, int W, int tsize) {
   return (int)(e + (e >> (tsize == 4 ? TileSwz<float>::v : TileSwz<double>::v)) + 1);
 }
 
-long long sweep_fbuf_complex(int K, int J, int tsize) {
+long long sweep_fbuf_complex(int K, int NB, int J, int tsize) {
+  if (NB > 0) return (long long)J * 2 * (tsize == 4 ? fft_stride<float>(NB) : fft_stride<double>(NB));
   const int fs = tsize == 4 ? fft_stride<float>(K) : fft_stride<double>(K);
   const bool pow2 = (K & (K - 1)) == 0;
   return (long long)J * 2 * fs * (pow2 ? 1 : 2);
+}
+
+int bluestein_pow2(int K) {
+  // outputs m = 0 .. H-1 (H = (K - 1) / 2 + 1) are used; the filter needs lags -(K-1) .. H-1
+  const int H = (K - 1) / 2 + 1;
+  int NB = 1;
+  while (NB < K - 1 + H) NB <<= 1;
+  return NB;
+}
+
+int bluestein_len(int K) {
+  if (K < 2 || (K & (K - 1)) == 0) return 0;
+  // direct passes: per element R reads and one write per pass (radices as in the plan:
+  // 4s, one 2, odd primes)
+  double direct = 0.0;
+  int r = K;
+  while (r % 4 == 0) { direct += 5; r /= 4; }
+  if (r % 2 == 0) { direct += 3; r /= 2; }
+  for (int p = 3; p <= r; p += 2)
+    while (r % p == 0) { direct += p + 1; r /= p; }
+  const int NB = bluestein_pow2(K);
+  const int lg = 31 - __builtin_clz(NB);
+  // Bluestein: two FFTs of (lg + 3) / 4 in-register passes (a read and a write each), the
+  // filter product, per entry of NB; the chirp products per entry of K
+  const double blue = (double)NB / K * (2.0 * 2.0 * ((lg + 3) / 4) + 2.0) + 2.0;
+  return blue < 0.8 * direct ? NB : 0;
 }
 
 // Warp-FFT path (FP32, 32 <= K <= 1024): X rows of K + L complex for every job of the
@@ -1154,11 +1284,11 @@ size_t sweep_smem_bytes_fbuf(int M, int W, long long fbuf_complex, int tsize) {
   return off;
 }
 
-size_t sweep_smem_bytes(int M, int n, int K, int W, int J, int tsize, bool strided) {
+size_t sweep_smem_bytes(int M, int n, int K, int NB, int W, int J, int tsize, bool strided) {
   (void)n;
   (void)strided;
   size_t off = ((size_t)sweep_tile_elems(M, W, tsize) * tsize + 15) & ~(size_t)15;
-  off += (size_t)sweep_fbuf_complex(K, J, tsize) * 2 * tsize;
+  off += (size_t)sweep_fbuf_complex(K, NB, J, tsize) * 2 * tsize;
   off += ((size_t)W * kMaxN * tsize + 15) & ~(size_t)15;
   off += 2 * (((size_t)W * tsize + 15) & ~(size_t)15);
   off += 2 * 32 * sizeof(double);

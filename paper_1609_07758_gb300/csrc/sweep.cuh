@@ -69,6 +69,14 @@ struct SweepParams {
   int radix_log[8];
   int radix_q[8];
   int pow2;
+  // Bluestein (chirp-z) form of a general-K DFT (nb > 0): with c_j = exp(-i pi j^2 / K),
+  //   X_m = c_m sum_j (x_j c_j) conj(c_{m-j}),   m < (K - 1) / 2 + 1 (the outputs used),
+  // a circular convolution of length nb = 2^nb_log (bluestein_pow2) done by an in-place
+  // power-of-two FFT (radices nb_radix), a product with the transformed filter and the
+  // inverse network.  Its tables follow the 2K DST twiddles in tw: exp(-i pi t / nb)
+  // (2 nb), c_j (K), and the filter's transform / nb in the FFT's output order (nb).
+  int nb, nb_log, nb_npass;
+  int nb_radix[4];
   int jobs_per_batch;
   long long fbuf_complex;     // complex elements of the FFT region (batched buffers or X + transposes)
   int wfft;                   // 1: warp-register FFT path (FP32, 32 <= K <= 1024)
@@ -84,10 +92,20 @@ struct SweepParams {
 cudaError_t launch_sweep_f32(const SweepParams& p, cudaStream_t s);
 cudaError_t launch_sweep_f64(const SweepParams& p, cudaStream_t s);
 
-// Shared-memory bytes a sweep needs for (M, n, K, W, J) in precision of size tsize.
-size_t sweep_smem_bytes(int M, int n, int K, int W, int J, int tsize, bool strided);
+// Shared-memory bytes a sweep needs for (M, n, K, W, J) in precision of size tsize; NB is
+// the Bluestein length of the sweep's transforms (0: power-of-two or direct passes).
+size_t sweep_smem_bytes(int M, int n, int K, int NB, int W, int J, int tsize, bool strided);
 int sweep_tile_elems(int M, int W, int tsize);
-long long sweep_fbuf_complex(int K, int J, int tsize);   // doubled (ping-pong) unless K = 2^m
+// complex entries of the FFT region: J jobs x 2 FFTs of K (doubled for the ping-pong of
+// the direct passes unless K = 2^m) or of NB (Bluestein, in place)
+long long sweep_fbuf_complex(int K, int NB, int J, int tsize);
+// Bluestein convolution length for K: the smallest power of two NB >= K - 1 + H, H =
+// (K - 1) / 2 + 1, so that the outputs m < H a DST needs are free of circular wrap-around.
+int bluestein_pow2(int K);
+// Bluestein length chosen for K (0: K is a power of two or its direct mixed-radix passes
+// are cheaper): bluestein_pow2(K) when two FFTs of that length cost less than 0.8 x the
+// direct passes (counting shared-memory reads and writes per element).
+int bluestein_len(int K);
 int wfft_row_stride(int K);
 long long wfft_fbuf_complex(int W, int n, int K, int nwarps);
 size_t sweep_smem_bytes_fbuf(int M, int W, long long fbuf_complex, int tsize);

@@ -85,6 +85,54 @@ def test_transform1d_matches_oracle(dtype, tol, n, K, lines):
     assert rel_l2(out.cpu().numpy(), ref) <= tol
 
 
+def bluestein_pow2(K):
+    """Smallest power of two >= K - 1 + H, H = (K - 1) // 2 + 1 (the DST's outputs m < H)."""
+    nb = 1
+    while nb < K - 1 + (K - 1) // 2 + 1:
+        nb *= 2
+    return nb
+
+
+@pytest.mark.parametrize("fft", ["direct", "bluestein"])
+@pytest.mark.parametrize("dtype,tol", [(0, 1e-13), (1, 1e-5)])
+@pytest.mark.parametrize("n,K,lines", [(1, 3, 4), (2, 7, 3), (3, 37, 4), (9, 97, 3), (2, 431, 2), (4, 600, 2),
+                                       (1, 1021, 2)])
+def test_bluestein_and_direct_transforms_match_oracle(monkeypatch, fft, dtype, tol, n, K, lines):
+    """Both forms of a K-point DFT with K not a power of two: the direct mixed-radix passes
+    over the prime factors of K and the Bluestein (chirp-z) convolution of power-of-two
+    length (smallest NB = 4 at K = 3; NB = 1024 < 2K - 1 at K = 600).  HOFEM_FFT forces
+    the form; the plan reports the FFT length it runs."""
+    monkeypatch.setenv("HOFEM_FFT", fft)
+    X = 0.9
+    plan = H().Plan(2, [K, K], n, [X, X], dtype)
+    assert plan.info().fft_len[0] == (K if fft == "direct" else bluestein_pow2(K))
+    s = spectrum.spectrum(n, K, X)
+    S = s.dense_S()
+    M = n * K - 1
+    rng = np.random.default_rng(7 * K + n)
+    y = rng.standard_normal((lines, M))
+    out = torch.zeros(lines, M, dtype=torch.float64, device="cuda")
+    fac = np.sqrt(s.norm / K)
+    plan.transform1d(0, 0, dev(y), out, lines)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), s.forward(y, S) * fac) <= tol
+    c = rng.standard_normal((lines, M))
+    plan.transform1d(0, 1, dev(c), out, lines)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), s.inverse(c / fac, S)) <= tol
+
+
+def test_fft_form_follows_the_cost_of_the_prime_factors():
+    """Default choice: power-of-two K and K with small prime factors keep the direct passes;
+    K with a large prime factor runs Bluestein (37, 431, 509 = primes; 4 * 4 * 29 = 464 is
+    near the break-even and stays direct)."""
+    for K, blue in ((1024, False), (105, False), (250, False), (2187, False), (464, False), (37, True),
+                    (431, True), (509, True), (2 * 3 * 71, True)):
+        plan = H().Plan(2, [K, 4], 2, [1.0, 1.0], 1)
+        assert plan.info().fft_len[0] == (bluestein_pow2(K) if blue else K), K
+        assert plan.info().fft_len[1] == 4
+
+
 SOLVE_CASES = [
     # N, n, K, X, alpha, nrhs
     (2, 1, [16, 8], [1.0, 2.0], 0.0, 2),
@@ -101,6 +149,9 @@ SOLVE_CASES = [
     (2, 5, [33, 20], [1.0, 1.0], 0.5, 1),
     (2, 8, [250, 3], [2.0, 0.6], 0.0, 1),
     (3, 3, [6, 5, 9], [1.0, 1.0, 1.0], 0.0, 1),
+    # prime K: Bluestein convolutions (97, 61, 31 on the strided middle axis of a 3D grid)
+    (2, 3, [97, 61], [1.0, 1.4], 0.0, 2),
+    (3, 2, [13, 31, 7], [1.0, 0.8, 1.2], 0.5, 1),
 ]
 
 
