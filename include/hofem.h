@@ -144,10 +144,18 @@ hofem_status hofem_plan(int N, const int* K, int n, const double* X, int dtype, 
 hofem_status hofem_plan_orders(int N, const int* K, const int* n, const double* X, int dtype, double alpha,
                                hofem_plan_t* out);
 
-/* Refined dtypes only: iters = residual/correction steps after the first low-precision
- * solve (0..100; default FP32 2 when every K is a power of two, else 3; BF16 and FP16 8);
- * tol > 0 additionally stops early once ||delta||/||u|| <= tol, which synchronises the
- * stream once per step.  tol = 0 keeps a fixed count (capturable). */
+/* Refined dtypes only: iters = most residual/correction steps after the first
+ * low-precision solve (0..100); tol > 0 stops once ||delta||_2 / ||u||_2 <= tol for every
+ * right-hand side, reading two doubles per right-hand side on the host after each step
+ * (one stream synchronisation per step), and a solve that ends above tol returns
+ * HOFEM_ERR_NOT_CONVERGED; tol = 0 runs exactly iters steps.
+ * Default: tol = 1e-12 with iters = 10 (FP32) or 16 (BF16, FP16).  The error after a
+ * step measured below its update norm, while the steps needed depend on the right-hand
+ * side (2D n = 9, K = 1024: 2 for a smooth one, 4 for N(0,1)).
+ * A solve issued into a capturing stream (CUDA graph capture) cannot synchronise: with
+ * tol > 0 it runs the plan's fixed capture count, by default FP32 2 when every K is a
+ * power of two, else 3, BF16 and FP16 8 (set by a call with tol = 0, which also fixes the
+ * count of uncaptured solves). */
 hofem_status hofem_set_refinement(hofem_plan_t plan, int iters, double tol);
 
 /* The (n+1)-point Gauss-Legendre quadrature points of the load vector along `axis`
@@ -218,7 +226,8 @@ hofem_status hofem_reserve(hofem_plan_t plan, int nrhs);
 
 /* u = A^{-1} f for nrhs right-hand sides (algorithm (a), Sect. 2 par. 4).  f, u: device
  * FP64 arrays (nrhs, M_1..M_N); u is overwritten; f is not modified.  f == u (in place)
- * is allowed for unrefined dtypes only. */
+ * is allowed for unrefined dtypes only.  Refined dtypes follow hofem_set_refinement (by
+ * default one stream synchronisation per correction step outside graph capture). */
 hofem_status hofem_solve(hofem_plan_t plan, const double* f, double* u, int nrhs, void* stream);
 
 /* r = A u: the matrix-free FP64 operator of Eq. bvp glob 2 (stiffness applied to

@@ -88,8 +88,9 @@ struct hofem_plan_s {
   double* tmp64[4] = {nullptr, nullptr, nullptr, nullptr};
   double* norms = nullptr;       // 2 per rhs
   double* h_norms = nullptr;     // pinned mirror
-  int refine_iters = 2;
-  double refine_tol = 0.0;
+  int refine_iters = 2;          // fixed count (refine_tol = 0) or most corrections
+  double refine_tol = 0.0;       // > 0: stop once ||delta|| / ||u|| <= refine_tol
+  int capture_iters = 2;         // fixed count of a solve issued into a capturing stream
   hofem_info info{};
   size_t table_bytes = 0;
   // profiling: event pairs recorded around launches, folded into per-kind totals on query
@@ -1016,15 +1017,21 @@ hofem_status hofem_plan_orders(int N, const int* K, const int* ns, const double*
     delete p;
     return st;
   }
-  // default correction steps, measured to reach <= 5e-13 for n <= 9: FP32 2 when every K
-  // is a power of two, 3 otherwise (the prime-length passes round a little worse; 512
-  // problems with n = 2..8, K = 32..512: worst 5.4e-12 after 2 steps, 3.3e-13 after 3);
-  // BF16 and FP16 8 (4-8 needed at n = 8-9, K = 64-1024)
+  // Default refinement: corrections until ||delta|| / ||u|| <= 1e-12 (measured: the error
+  // after a correction stays below its update norm), at most 10 (FP32) or 16 (BF16,
+  // FP16).  The contraction per step depends on the right-hand side: a rough residual is
+  // solved accurately in its high modes only, a smooth one throughout, so steps alternate
+  // between ~0.1-0.9 and ~1e-5 (2D n = 9, K = 1024, N(0,1) RHS: 2.4e-12 after 2, 6e-15
+  // after 4; smooth RHS: 4.9e-13 after 2).  A capturing stream cannot be read by the host,
+  // so a captured solve runs a fixed count instead: FP32 2 when every K is a power of two,
+  // else 3 (512 problems, n = 2..8, K = 32..512, N(0,1): worst 7.5e-14 after 3), BF16 and
+  // FP16 8.
   bool all_pow2 = true;
   for (int i = 0; i < N; ++i) all_pow2 = all_pow2 && is_pow2(K[i]);
-  p->refine_iters = dtype == HOFEM_FP32_REFINED                                    ? (all_pow2 ? 2 : 3)
-                    : (dtype == HOFEM_BF16_REFINED || dtype == HOFEM_FP16_REFINED) ? 8
-                                                                                    : 0;
+  const bool half = dtype == HOFEM_BF16_REFINED || dtype == HOFEM_FP16_REFINED;
+  p->capture_iters = dtype == HOFEM_FP32_REFINED ? (all_pow2 ? 2 : 3) : half ? 8 : 0;
+  p->refine_iters = dtype == HOFEM_FP32_REFINED ? 10 : half ? 16 : 0;
+  p->refine_tol = p->refined ? 1e-12 : 0.0;
   for (int i = 0; i < N; ++i) element_load_table(ns[i], &p->load_T[i], &p->load_xi[i]);
   hofem_info& inf = p->info;
   inf.N = N;
@@ -1053,6 +1060,7 @@ hofem_status hofem_set_refinement(hofem_plan_t p, int iters, double tol) {
   if (iters < 0 || iters > 100 || !(tol >= 0.0)) return fail(HOFEM_ERR_INVALID_ARG, "iters in 0..100, tol >= 0");
   p->refine_iters = iters;
   p->refine_tol = tol;
+  if (tol == 0.0) p->capture_iters = iters;
   p->info.refine_iters = iters;
   return HOFEM_OK;
 }
@@ -1261,7 +1269,11 @@ hofem_status hofem_solve(hofem_plan_t p, const double* f, double* u, int nrhs, v
     return st;
   }
   if ((st = reserve(p, nrhs)) != HOFEM_OK) return st;
-  const int iters = refined ? p->refine_iters : 0;
+  // the tolerance test reads the norms on the host, which a capturing stream cannot do
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  HOFEM_CUDA(cudaStreamIsCapturing(s, &cap), "cudaStreamIsCapturing");
+  const bool adaptive = refined && p->refine_tol > 0.0 && cap == cudaStreamCaptureStatusNone;
+  const int iters = !refined ? 0 : (p->refine_tol > 0.0 && !adaptive) ? p->capture_iters : p->refine_iters;
   // norms[2 r + 1] = ||u||^2 of the first solve, norms[2 r] = ||delta||^2 of the last step
   if (iters > 0) HOFEM_CUDA(cudaMemsetAsync(p->norms, 0, 2 * (size_t)nrhs * sizeof(double), s), "memset norms");
   if ((st = solve_once(p, f, u, nrhs, false, false, iters > 0 ? p->norms : nullptr, 1, s)) != HOFEM_OK) return st;
@@ -1272,7 +1284,7 @@ hofem_status hofem_solve(hofem_plan_t p, const double* f, double* u, int nrhs, v
     HOFEM_CUDA(cudaMemset2DAsync(p->norms, 2 * sizeof(double), 0, sizeof(double), nrhs, s), "memset norms");
     if ((st = solve_once(p, p->r64, u, nrhs, false, true, p->norms, 0, s)) != HOFEM_OK) return st;
     ++done;
-    if (p->refine_tol > 0.0) {
+    if (adaptive) {
       HOFEM_CUDA(cudaMemcpyAsync(p->h_norms, p->norms, 2 * (size_t)nrhs * sizeof(double), cudaMemcpyDeviceToHost, s),
                  "copy norms");
       HOFEM_CUDA(cudaStreamSynchronize(s), "stream sync (refinement tolerance)");
@@ -1284,7 +1296,7 @@ hofem_status hofem_solve(hofem_plan_t p, const double* f, double* u, int nrhs, v
       if (worst <= p->refine_tol) { converged = true; break; }
     }
   }
-  if (p->refine_tol <= 0.0) {
+  if (!adaptive) {
     converged = true;   // fixed iteration count
     if (iters > 0)
       HOFEM_CUDA(cudaMemcpyAsync(p->h_norms, p->norms, 2 * (size_t)nrhs * sizeof(double), cudaMemcpyDeviceToHost, s),
@@ -1292,7 +1304,7 @@ hofem_status hofem_solve(hofem_plan_t p, const double* f, double* u, int nrhs, v
   }
   p->info.iterations = done;
   p->info.converged = converged ? 1 : 0;
-  if (refined && p->refine_tol > 0.0 && !converged)
+  if (adaptive && !converged)
     return fail(HOFEM_ERR_NOT_CONVERGED, "refinement did not reach the tolerance");
   return HOFEM_OK;
 }

@@ -230,6 +230,35 @@ def test_fp64_solve_in_place():
     assert rel_l2(fd.cpu().numpy(), ref) <= 1e-12
 
 
+def test_default_refinement_stops_on_its_tolerance_and_capture_runs_the_fixed_count():
+    """Outside graph capture the default refinement stops once ||delta|| / ||u|| <= 1e-12;
+    a solve captured into a CUDA graph cannot read the norms and runs the plan's fixed
+    count instead (3 here: K = 48 is not a power of two)."""
+    n, K = 4, [32, 48]
+    plan = H().Plan(2, K, n, [1.0, 0.6], H().HOFEM_FP32_REFINED)
+    assert plan.info().refine_iters == 10
+    Ms = [n * k - 1 for k in K]
+    f = np.random.default_rng(4).standard_normal([1] + Ms)
+    ref = osolve.solve_tensor(f, [n, n], K, [1.0, 0.6])
+    fd = dev(f)
+    ud = torch.zeros_like(fd)
+    plan.reserve(1)
+    plan.solve(fd, ud, 1)
+    torch.cuda.synchronize()
+    info = plan.info()
+    assert info.converged == 1 and 1 <= info.iterations <= 10 and info.last_rel_update <= 1e-12
+    assert rel_l2(ud.cpu().numpy(), ref) <= 1e-12
+    u2 = torch.zeros_like(fd)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.solve(fd, u2, 1, torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    info = plan.info()
+    assert info.iterations == 3 and info.converged == 1
+    assert rel_l2(u2.cpu().numpy(), ref) <= 1e-12
+
+
 def test_refinement_reports_its_progress():
     n, K = 4, [32, 32]
     plan = H().Plan(2, K, n, [1.0, 1.0], H().HOFEM_FP32_REFINED)

@@ -72,6 +72,32 @@ def test_2d_n9_k1024_fp64_and_mixed_match_oracle():
         plan.close()
 
 
+def test_2d_n9_k1024_gaussian_rhs_refines_to_its_tolerance():
+    """An N(0,1) right-hand side with anisotropic cells (X = (0.5, 4)) needs more
+    correction steps than the smooth one above: FP32 rounding of a rough residual leaves
+    its low modes inexact.  The default refinement stops on its update norm and meets
+    1e-12 against the oracle; two fixed corrections do not."""
+    from paper_1609_07758_gb300 import inputs
+    n, K, X = 9, 1024, [0.5, 4.0]
+    M = n * K - 1
+    f = inputs.gaussian_rhs(6, (1, M, M))
+    ref = osolve.solve_tensor(f, [n, n], [K, K], X)
+    fd = torch.from_numpy(f).cuda()
+    plan = H().Plan(2, [K, K], n, X, H().HOFEM_FP32_REFINED)
+    ud = torch.zeros_like(fd)
+    plan.solve(fd, ud, 1)
+    torch.cuda.synchronize()
+    info = plan.info()
+    err = rel_l2(ud.cpu().numpy(), ref)
+    plan.set_refinement(2)
+    plan.solve(fd, ud, 1)
+    torch.cuda.synchronize()
+    err2 = rel_l2(ud.cpu().numpy(), ref)
+    print(f"default: {info.iterations} steps, rel L2 vs oracle {err:.2e}; two fixed steps: {err2:.2e}")
+    assert info.converged == 1 and info.iterations >= 3 and info.last_rel_update <= 1e-12
+    assert err <= 1e-12 < err2
+
+
 def test_3d_n4_k128_mixed_matches_oracle():
     from paper_1609_07758_gb300 import inputs
     n, K = 4, 128
@@ -138,6 +164,10 @@ def test_batched_512_problems_refined():
         p64.close()
     print(f"  max rel L2 vs FP64 over 512 problems {worst:.3e}")
     assert worst <= 1e-12
+    # captured solves run the fixed count: 2 corrections when K is a power of two, else 3
+    for i, q in enumerate(probs):
+        pw = all(k & (k - 1) == 0 for k in q["K"])
+        assert b.plan_info(i).iterations == (2 if pw else 3), i
     size = [q["nrhs"] * (q["n"] * q["K"][0] - 1) ** 2 for q in probs]
     for i in (int(np.argmin(size)), int(np.argmax(size)), 100):
         q = probs[i]
