@@ -329,6 +329,10 @@ std::mutex g_tune_mu;
 std::map<TuneKey, std::pair<int, int>> g_tuned;
 bool g_tune_loaded = false;
 thread_local int g_force_a = 0, g_force_b = 0;   // candidate under measurement (0: none)
+// A sweep's launch shape stores the DST batch J plus this flag when the per-frequency
+// mixing reads its table rows from global memory (L2) instead of staging the table
+// through shared memory in chunks (the better form when a CTA holds few lines).
+constexpr int kMixDirectFlag = 1 << 16;
 
 bool tuned_lookup(const TuneKey& k, int* a, int* b) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -383,11 +387,18 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   } else if (g_force_a > 0) {
     W = g_force_a;
     J = g_force_b;
-  } else if (!(tuned_lookup(key, &W, &J) &&
-               sweep_smem_bytes(A.h.M, A.h.n, A.h.K, NB, W, J, tsize, strided) <= kSmemLimit) &&
-             !choose_sweep(A.h.M, A.h.n, A.h.K, NB, tsize, lines, strided, &W, &J)) {
+  } else if (tuned_lookup(key, &W, &J) &&
+             sweep_smem_bytes(A.h.M, A.h.n, A.h.K, NB, W, J % kMixDirectFlag, tsize, strided) <= kSmemLimit) {
+  } else if (choose_sweep(A.h.M, A.h.n, A.h.K, NB, tsize, lines, strided, &W, &J)) {
+    // mixing rows straight from L2 when few lines per CTA would reuse a staged table
+    if (W <= 4) J += kMixDirectFlag;
+  } else {
     return fail(HOFEM_ERR_UNSUPPORTED, "no launch configuration fits shared memory for this axis");
   }
+  // J carries the mixing form: J / kMixDirectFlag = 1 reads the rows from global memory
+  int mix_direct = J / kMixDirectFlag;
+  J %= kMixDirectFlag;
+  if (const char* md = getenv("HOFEM_MIX_DIRECT")) mix_direct = md[0] == '1' ? 1 : 0;
   P.outer = nrhs * g.outer_per_rhs;
   P.inner = g.inner;
   P.outer_per_rhs = g.outer_per_rhs;
@@ -453,6 +464,7 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
     P.nb_log = 31 - __builtin_clz(P.nb);
   }
   P.jobs_per_batch = J;
+  P.mix_direct = mix_direct;
   P.wfft = wfft ? 1 : 0;
   P.wf_xs = wfft ? wfft_row_stride(A.h.K) : 0;
   P.fbuf_complex = wfft ? wfft_fbuf_complex(W, A.h.n, A.h.K, nwarps) : sweep_fbuf_complex(A.h.K, P.nb, J, tsize);
@@ -808,9 +820,10 @@ hofem_status tune_plan(hofem_plan_s* p, int nrhs, cudaStream_t s, int* measured)
         --Jmax;
       if (Jmax < 1) continue;
       // the largest DST batch, and halves of it (less shared memory, more batches)
-      for (int J = Jmax; J >= 1 && J * 4 >= Jmax; J = (J == 1 ? 0 : (J + 1) / 2)) {
+      for (int J = Jmax; J >= 1 && J * 4 >= Jmax; J = (J == 1 ? 0 : (J + 1) / 2))
+      for (int direct = 0; direct <= 1; ++direct) {
         g_force_a = W;
-        g_force_b = J;
+        g_force_b = J + direct * kMixDirectFlag;
         bool ok = false;
         const double ms = time_launches(s, [&]() {
           return run_sweep(p, w.axis, w.mode, f64, w.in, w.in_fmt, w.out, w.out_fmt, w.acc,
@@ -818,7 +831,7 @@ hofem_status tune_plan(hofem_plan_s* p, int nrhs, cudaStream_t s, int* measured)
         }, &ok);
         g_force_a = g_force_b = 0;
         ++*measured;
-        if (ok && ms < best) { best = ms; bw = W; bj = J; }
+        if (ok && ms < best) { best = ms; bw = W; bj = J + direct * kMixDirectFlag; }
       }
     }
     if (bw > 0) {

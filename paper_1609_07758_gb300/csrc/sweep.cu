@@ -725,7 +725,7 @@ __device__ void forward_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
   __syncthreads();
   // mixing: w_k = G_k xhat_k / (2K)  (the DST outputs above are 2 x DST)
   mix_dispatch<T, true>(tl, W, n, K, mix, P.mixNP, evec, tsave, (T)(0.5 / K), (T)(1.0 / K),
-                        reinterpret_cast<T*>(fbuf), 2 * P.fbuf_complex);
+                        reinterpret_cast<T*>(fbuf), P.mix_direct ? 0 : 2 * P.fbuf_complex);
   __syncthreads();
 }
 
@@ -735,7 +735,7 @@ __device__ void inverse_transform(const Tile<T>& tl, typename Cx<T>::type* fbuf,
                                   const T* __restrict__ evec, const typename Cx<T>::type* __restrict__ tw) {
   // mixing: xhat_k = G_k^T w_k / 2 (the DST below returns 2 x DST); g = E^T w_0
   mix_dispatch<T, false>(tl, W, n, K, mix, P.mixNP, evec, gsave, (T)0.5, (T)1.0,
-                         reinterpret_cast<T*>(fbuf), 2 * P.fbuf_complex);
+                         reinterpret_cast<T*>(fbuf), P.mix_direct ? 0 : 2 * P.fbuf_complex);
   __syncthreads();
   const int logK = 31 - __clz(K);
   const int logW = 31 - __clz(W);

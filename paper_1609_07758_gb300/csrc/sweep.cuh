@@ -77,6 +77,7 @@ struct SweepParams {
   // (2 nb), c_j (K), and the filter's transform / nb in the FFT's output order (nb).
   int nb, nb_log, nb_npass;
   int nb_radix[4];
+  int mix_direct;             // 1: mixing rows read from global memory (L2), not staged
   int jobs_per_batch;
   long long fbuf_complex;     // complex elements of the FFT region (batched buffers or X + transposes)
   int wfft;                   // 1: warp-register FFT path (FP32, 32 <= K <= 1024)
