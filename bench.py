@@ -281,6 +281,7 @@ def extra_paths(hofem, torch, f, u, stream, args):
     out["heat_step_refined_ms"] = time_ms(lambda: ph.heat_steps(uh, 1, 1, stream=stream))
     # variable coefficient a = 1 + sin(pi x) cos(3 y) / 2 at the Gauss points; PCG to 1e-10
     pr = hofem.Plan(2, K2, N_ORDER, X2, hofem.HOFEM_FP32_REFINED)
+    pr.set_refinement(2)   # a fixed preconditioner; CG itself drives the error to its tolerance
     x = torch.tensor(pr.quadrature_points(0), dtype=torch.float64, device="cuda")
     aq = 1.0 + 0.5 * torch.outer(torch.sin(torch.pi * x), torch.cos(3.0 * x))
     r = torch.empty_like(u[0])
