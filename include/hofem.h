@@ -151,7 +151,10 @@ hofem_status hofem_plan_orders(int N, const int* K, const int* n, const double* 
  * HOFEM_ERR_NOT_CONVERGED; tol = 0 runs exactly iters steps.
  * Default: tol = 1e-12 with iters = 10 (FP32) or 16 (BF16, FP16).  The error after a
  * step measured below its update norm, while the steps needed depend on the right-hand
- * side (2D n = 9, K = 1024: 2 for a smooth one, 4 for N(0,1)).
+ * side (2D n = 9, K = 1024: 2 for a smooth one, 4 for N(0,1)).  Orders n <= 11 converge
+ * (3-4 steps at K = 8..64); equispaced n >= 12 elements are too ill-conditioned for an
+ * FP32 solve to contract to 1e-12, so their default refined solves end with
+ * HOFEM_ERR_NOT_CONVERGED (u then holds the last iterate; use HOFEM_FP64).
  * A solve issued into a capturing stream (CUDA graph capture) cannot synchronise: with
  * tol > 0 it runs the plan's fixed capture count, by default FP32 2 when every K is a
  * power of two, else 3, BF16 and FP16 8 (set by a call with tol = 0, which also fixes the

@@ -259,6 +259,31 @@ def test_default_refinement_stops_on_its_tolerance_and_capture_runs_the_fixed_co
     assert rel_l2(u2.cpu().numpy(), ref) <= 1e-12
 
 
+@pytest.mark.parametrize("n", [10, 11, 12, 16])
+def test_refined_orders_converge_up_to_11_and_report_failure_above(n):
+    """Equispaced elements of order n >= 12 are too ill-conditioned for FP32 corrections to
+    reach the default tolerance: the solve says so (HOFEM_ERR_NOT_CONVERGED) instead of
+    returning an inaccurate u silently; n = 10, 11 converge to the oracle."""
+    K = [8, 8]
+    plan = H().Plan(2, K, n, [1.0, 1.0], H().HOFEM_FP32_REFINED)
+    Ms = [n * k - 1 for k in K]
+    f = np.random.default_rng(n).standard_normal([1] + Ms)
+    fd = dev(f)
+    ud = torch.zeros_like(fd)
+    if n >= 12:
+        with pytest.raises(H().HofemError) as e:
+            plan.solve(fd, ud, 1)
+        torch.cuda.synchronize()
+        assert e.value.status == 5 and "tolerance" in str(e.value)
+        assert plan.info().converged == 0 and plan.info().iterations == 10
+        return
+    plan.solve(fd, ud, 1)
+    torch.cuda.synchronize()
+    assert plan.info().converged == 1
+    ref = osolve.solve_tensor(f, [n, n], K, [1.0, 1.0])
+    assert rel_l2(ud.cpu().numpy(), ref) <= 1e-12
+
+
 def test_refinement_reports_its_progress():
     n, K = 4, [32, 32]
     plan = H().Plan(2, K, n, [1.0, 1.0], H().HOFEM_FP32_REFINED)
