@@ -72,9 +72,10 @@ typedef struct {
   int K[3];                 /* elements per axis */
   int M[3];                 /* unknowns per axis, n K - 1 */
   int dtype;                /* hofem_dtype of the plan */
-  int refine_iters;         /* residual + correction steps per solve (refined dtypes) */
-  int iterations;           /* steps actually run by the last solve */
-  int converged;            /* 1 if the last solve met its tolerance (or ran its fixed count) */
+  int refine_iters;         /* most correction steps of a solve (tolerance mode) or its fixed
+                               count (refined dtypes; see hofem_set_refinement) */
+  int iterations;           /* correction steps actually run by the last solve */
+  int converged;            /* 1 if the last solve met its tolerance (or ran a fixed count) */
   double last_rel_update;   /* ||delta||_2 / ||u||_2 of the last correction, max over RHS
                                (valid after the caller synchronises the stream) */
   double plan_ms;           /* host wall time of hofem_plan */
