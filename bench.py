@@ -299,29 +299,69 @@ def extra_paths(hofem, torch, f, u, stream, args):
 
 
 def e2e_time(plan, f_host, f, stream, args, world, torch):
-    """ms per step through the C ABI from pinned host buffers: H2D f, solve, D2H u."""
+    """ms per step through the C ABI from pinned host buffers: every step copies its f to the
+    device, solves and copies its u back.  Returns (pipelined, serial): pipelined overlaps the
+    copies of neighbouring steps with the solve on two copy streams (double-buffered f and u
+    on the device: H2D of step i+1 and D2H of step i-1 run during the solve of step i); serial
+    runs copy, solve, copy on one stream.  Both time every step's copies."""
     fh = torch.from_numpy(f_host).pin_memory()
     uh = torch.empty_like(fh).pin_memory()
-    fd = torch.empty_like(f)
-    ud = torch.empty_like(f)
+    fd = [torch.empty_like(f), torch.empty_like(f)]
+    ud = [torch.empty_like(f), torch.empty_like(f)]
+    cin, cout = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()
+    ev_in, ev_solved, ev_out = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+    for b in range(2):                                  # buffers start free
+        ev_solved[b].record(stream)
+        ev_out[b].record(stream)
 
-    def e2e_step():
-        fd.copy_(fh, non_blocking=True)
-        plan.solve(fd, ud, 1, stream)
-        uh.copy_(ud, non_blocking=True)
+    def pipelined_step(i):
+        b = i % 2
+        cin.wait_event(ev_solved[b])                    # solve i-2 has finished reading fd[b]
+        with torch.cuda.stream(cin):
+            fd[b].copy_(fh, non_blocking=True)
+        ev_in[b].record(cin)
+        stream.wait_event(ev_in[b])
+        stream.wait_event(ev_out[b])                    # ud[b] of step i-2 is back on the host
+        plan.solve(fd[b], ud[b], 1, stream)
+        ev_solved[b].record(stream)
+        cout.wait_event(ev_solved[b])
+        with torch.cuda.stream(cout):
+            uh.copy_(ud[b], non_blocking=True)
+        ev_out[b].record(cout)
 
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
+    def serial_step():
+        fd[0].copy_(fh, non_blocking=True)
+        plan.solve(fd[0], ud[0], 1, stream)
+        uh.copy_(ud[0], non_blocking=True)
+
     steps = max(3, args.steps // 3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    for i in range(2):
+        pipelined_step(i)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0.record(stream)
+    cin.wait_event(e0)
+    for i in range(steps):
+        pipelined_step(i)
+    stream.wait_event(ev_out[(steps - 1) % 2])          # the last u is on the host
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_pipe = e0.elapsed_time(e1) / steps
+
+    for _ in range(2):
+        serial_step()
+    torch.cuda.synchronize()
     barrier(world)
     e0.record(stream)
     for _ in range(steps):
-        e2e_step()
+        serial_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    return max_over_ranks(e0.elapsed_time(e1) / steps, world)
+    ms_serial = e0.elapsed_time(e1) / steps
+    return max_over_ranks(ms_pipe, world), max_over_ranks(ms_serial, world)
 
 
 def main():
@@ -405,9 +445,9 @@ def main():
 
     # end to end through the C ABI with host buffers: H2D of f, solve, D2H of u, every step
     if args.no_e2e:
-        ms_e2e = float("nan")
+        ms_e2e = ms_e2e_serial = float("nan")
     else:
-        ms_e2e = e2e_time(plan, f_host, f, stream, args, world, torch)
+        ms_e2e, ms_e2e_serial = e2e_time(plan, f_host, f, stream, args, world, torch)
     extras = None
     if args.extras:
         extras = extra_paths(hofem, torch, f, u, stream, args)
@@ -462,7 +502,11 @@ def main():
         "kernels": kinds,
         "cpu_baseline": cpu,
         "e2e": None if args.no_e2e else {"value": job_throughput(UNKNOWNS, world, ms_e2e), "unit": UNIT,
-                                         "h2d_bytes_per_step": 8 * UNKNOWNS, "d2h_bytes_per_step": 8 * UNKNOWNS},
+                                         "h2d_bytes_per_step": 8 * UNKNOWNS, "d2h_bytes_per_step": 8 * UNKNOWNS,
+                                         "ms_per_step": ms_e2e,
+                                         "copies": "overlapped with the neighbouring steps' solves (2 copy streams)",
+                                         "serial": {"value": job_throughput(UNKNOWNS, world, ms_e2e_serial),
+                                                    "ms_per_step": ms_e2e_serial}},
         "gpu_launches": launches,
         **({"extras_ms": extras} if extras else {}),
         **({"batched": batched} if batched else {}),
