@@ -56,18 +56,26 @@ def test_2d_n2_k64_manufactured_with_noise():
 
 
 def test_2d_n9_k1024_fp64_and_mixed_match_oracle():
+    """In the launch configuration bench.py times (both plans autotuned at plan time, the mixed
+    plan with its fixed 2 corrections), and the mixed plan's verified default."""
     from paper_1609_07758_gb300 import inputs
     n, K = 9, 1024
     f = inputs.smooth_sine_rhs(2, n, K)
     ref = osolve.solve_tensor(f, [n, n], [K, K], [1.0, 1.0])
     fd = torch.from_numpy(f).cuda()
-    for dtype in (H().HOFEM_FP64, H().HOFEM_FP32_REFINED):
+    for dtype, fixed, tune in ((H().HOFEM_FP64, None, True), (H().HOFEM_FP32_REFINED, 2, True),
+                               (H().HOFEM_FP32_REFINED, None, False)):
         plan = H().Plan(2, [K, K], n, [1.0, 1.0], dtype)
+        if fixed:
+            plan.set_refinement(fixed)
+        if tune:
+            plan.autotune(1)
         ud = torch.zeros_like(fd)
         plan.solve(fd, ud, 1)
         torch.cuda.synchronize()
         err = rel_l2(ud.cpu().numpy(), ref)
-        print(f"dtype {dtype}: rel L2 vs oracle {err:.3e}")
+        print(f"dtype {dtype}, fixed corrections {fixed}, tuned {tune}: rel L2 vs oracle {err:.3e}, "
+              f"{plan.info().iterations} corrections")
         assert err <= 1e-12
         plan.close()
 
