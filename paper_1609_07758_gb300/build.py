@@ -25,13 +25,33 @@ def nvcc():
     return exe
 
 
+# Sources compiled more than once, each time with one macro: the sweep kernels' FP32 and
+# FP64 instantiations (the longest compile) build in parallel with the host helpers.
+PARTS = {"sweep.cu": ["HOFEM_SWEEP_PART=0", "HOFEM_SWEEP_PART=1", "HOFEM_SWEEP_PART=2"]}
+
+
 def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _compile(src, verbose=False, defines=()):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, *[f"-D{d}" for d in defines], "-c", src, "-o", obj]
+def jobs():
+    """(source, extra macro or None, object name) for every object of the library."""
+    out = []
+    for src in sources():
+        base = os.path.basename(src)[:-3]
+        parts = PARTS.get(os.path.basename(src))
+        if parts:
+            out += [(src, d, f"{base}_p{i}.o") for i, d in enumerate(parts)]
+        else:
+            out.append((src, None, base + ".o"))
+    return out
+
+
+def _compile(job, verbose=False, defines=()):
+    src, part, name = job
+    obj = os.path.join(BUILD, name)
+    extra = [part] if part else []
+    cmd = [nvcc(), *ARCH, *FLAGS, *[f"-D{d}" for d in (*defines, *extra)], "-c", src, "-o", obj]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     res = subprocess.run(cmd, capture_output=True, text=True)
@@ -55,8 +75,9 @@ def build(verbose=False, force=False, lib=None, defines=()):
         lib_t = os.path.getmtime(target)
         if all(os.path.getmtime(d) <= lib_t for d in deps):
             return target
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose, defines), srcs))
+    todo = jobs()
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(todo))) as ex:
+        results = list(ex.map(lambda j: _compile(j, verbose, defines), todo))
     if verbose:
         for _, log in results:
             sys.stderr.write(log)

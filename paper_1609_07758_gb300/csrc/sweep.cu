@@ -32,6 +32,14 @@
 
 #include "sweep.cuh"
 
+// The build compiles this file three times (HOFEM_SWEEP_PART = 0: host helpers and absmax;
+// 1: the FP32 kernel instantiations and their launcher; 2: the FP64 ones) so that the
+// instantiations compile in parallel; without the macro one object holds everything.
+#ifndef HOFEM_SWEEP_PART
+#define HOFEM_SWEEP_PART -1
+#endif
+#define HOFEM_SWEEP_HAS(k) (HOFEM_SWEEP_PART < 0 || HOFEM_SWEEP_PART == (k))
+
 namespace hofem {
 
 template <typename T> struct Cx;
@@ -856,7 +864,7 @@ __device__ __forceinline__ void wfft_core(float2 (&v)[32], float2* sg, int r, co
 }
 
 // Stage x_j = (a_j, b_j), j = 0..K-1 (x_0 = 0) of every job into X (row stride XS).
-__device__ void wfft_build_x(const Tile<float> tl, float2* X, int XS, int njobs, int W, int n, int K, bool inverse) {
+static __device__ void wfft_build_x(const Tile<float> tl, float2* X, int XS, int njobs, int W, int n, int K, bool inverse) {
   const int logK = 31 - __clz(K), logW = 31 - __clz(W);
   const int items = njobs << logK;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
@@ -913,7 +921,7 @@ __device__ __noinline__ void wfft_tasks(const Tile<float> tl, const float2* X, i
 // Inverse post-combine of one job (by one warp): D at rows of its components -> physical
 // v_{j-1/2} = D_{j-1} + P D_j + (-P)^{j-1} g (nodes are already in place).  Lanes own
 // contiguous j ranges and walk them downwards; each first reads the value below its range.
-__device__ void wfft_postcombine(const Tile<float> tl, const float* gsave, int njobs, int W, int n, int K) {
+static __device__ void wfft_postcombine(const Tile<float> tl, const float* gsave, int njobs, int W, int n, int K) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int logW = 31 - __clz(W);
   const int per = (K + 31) / 32;                // j values per lane
@@ -1212,6 +1220,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
   }
 }
 
+#if HOFEM_SWEEP_HAS(0)
 // Per-rhs max |x| (FP64 bit patterns of non-negative values order like the values).
 __global__ void absmax_kernel(const double* __restrict__ x, long long per_rhs, unsigned long long* amax) {
   const long long r = blockIdx.y;
@@ -1303,13 +1312,22 @@ int sweep_max_jobs(int K, int tsize, int threads) {
   return 1 << 20;
 }
 
+cudaError_t sweep_set_smem_limits_f32();
+cudaError_t sweep_set_smem_limits_f64();
+
 cudaError_t sweep_set_smem_limits() {
+  cudaError_t e = sweep_set_smem_limits_f32();
+  if (e == cudaSuccess) e = sweep_set_smem_limits_f64();
+  return e;
+}
+#endif  // part 0
+
+#if HOFEM_SWEEP_HAS(1)
+cudaError_t sweep_set_smem_limits_f32() {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e = cudaFuncSetAttribute(sweep_kernel<float, false, false>, a, 232448);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep_kernel<float, true, false>, a, 232448);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep_kernel<float, false, true>, a, 232448);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep_kernel<double, false, false>, a, 232448);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep_kernel<double, false, true>, a, 232448);
   return e;
 }
 
@@ -1319,11 +1337,21 @@ cudaError_t launch_sweep_f32(const SweepParams& p, cudaStream_t s) {
   else sweep_kernel<float, false, true><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
   return cudaGetLastError();
 }
+#endif  // part 1
+
+#if HOFEM_SWEEP_HAS(2)
+cudaError_t sweep_set_smem_limits_f64() {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<double, false, false>, a, 232448);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep_kernel<double, false, true>, a, 232448);
+  return e;
+}
 
 cudaError_t launch_sweep_f64(const SweepParams& p, cudaStream_t s) {
   if (p.pow2) sweep_kernel<double, false, false><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
   else sweep_kernel<double, false, true><<<(unsigned)p.ntiles, p.threads, p.smem_bytes, s>>>(p);
   return cudaGetLastError();
 }
+#endif  // part 2
 
 }  // namespace hofem
