@@ -286,7 +286,8 @@ void hofem_destroy(hofem_plan_t plan);
 
 /* Batched solves of independent problems of uneven K, n, X and nrhs: one plan per problem
  * with its workspace reserved up front.  The first hofem_batch_solve captures every
- * problem's solve (the refined dtypes with their fixed step count) into one CUDA graph
+ * problem's solve (refined dtypes with the plan's fixed capture count: FP32 2 when every
+ * K is a power of two, else 3; BF16 and FP16 8; see hofem_set_refinement) into one CUDA graph
  * whose branches spread the problems over up to 16 streams, so independent problems run
  * concurrently; later calls with the same pointer arrays relaunch that graph (other
  * pointers recapture it).  Synchronous plan; errors of one problem name its index in
