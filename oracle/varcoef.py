@@ -10,7 +10,10 @@ x_i = x_{i, j_i - 1} + (xi_i + 1) h_i / 2,
 
 evaluated with the (n+1)-point Gauss-Legendre rule per direction (the load vector's rule,
 Sect. 2 par. 5), a given by its values at those points.  For a = 1 it is the operator of
-Eq. bvp glob 2 with alpha = 0 (pinned in tests/test_oracle_varcoef.py).  Plain numpy:
+Eq. bvp glob 2 with alpha = 0.  Pins (tests/test_oracle_varcoef.py): that a = 1
+reduction; entrywise agreement with the exact rational integration of an affine a (which
+the rule integrates exactly) on a non-square grid of elements; and the O(h^{n+1}) dof
+convergence of a manufactured solution with a non-separable a.  Plain numpy:
 element loops vectorised with einsum, scatter-add through the element dof map.
 """
 import numpy as np
@@ -39,13 +42,23 @@ def _basis_and_derivative(n, xi):
     return B, D
 
 
+def coefficient_at_points(aq, Ks, G):
+    """a[j1, j2, g, h]: the value of a at Gauss point g (axis 1) and h (axis 2) of element
+    (j1, j2), from aq whose row index is the axis-1 point (j1 G + g) and whose column index
+    is the axis-2 point (j2 G + h).  Pinned by the exact integration of an affine a with
+    different slopes along the two axes (tests/test_oracle_varcoef.py)."""
+    return aq.reshape(Ks[0], G, Ks[1], G).transpose(0, 2, 1, 3)
+
+
 def element_matrices(n, Ks, Xs, aq):
-    """(K1, K2, (n+1)^2, (n+1)^2) element matrices; aq: (K1 (n+1), K2 (n+1)) values of a."""
+    """(K1, K2, (n+1)^2, (n+1)^2) element matrices; aq: (K1 (n+1), K2 (n+1)) values of a.
+
+    Local index p = a (n+1) + b: basis e_a along axis 1 times e_b along axis 2."""
     xi, w = np.polynomial.legendre.leggauss(n + 1)
     B, D = _basis_and_derivative(n, xi)
     G = n + 1
     s1, s2 = 4.0 * (Ks[0] / Xs[0]) ** 2, 4.0 * (Ks[1] / Xs[1]) ** 2
-    a = aq.reshape(Ks[0], G, Ks[1], G).transpose(0, 2, 1, 3) * np.outer(w, w)[None, None]
+    a = coefficient_at_points(aq, Ks, G) * np.outer(w, w)[None, None]
     # gradients of the basis at the quadrature points, per reference direction
     Gx = np.einsum("ga,hb->ghab", D, B).reshape(G, G, G * G)
     Gy = np.einsum("ga,hb->ghab", B, D).reshape(G, G, G * G)
