@@ -245,9 +245,10 @@ hofem_status hofem_apply(hofem_plan_t plan, const double* u, double* r, int nrhs
  * The operator's intermediate arrays (2 for N = 2, 4 for N = 3, each nrhs x unknowns
  * doubles) live in one fixed 32 MiB device array inside the library, resident on every
  * GPU that loads it until the process exits; nrhs x unknowns above 2,097,152 (N = 2) or
- * 1,048,576 (N = 3) returns HOFEM_ERR_INVALID_ARG.  The first call on each device looks
- * up that array's device address (cudaGetSymbolAddress) with the device current: make
- * that first call before any stream capture.  All calls share the array, so calls whose
+ * 1,048,576 (N = 3) returns HOFEM_ERR_INVALID_ARG.  Every call outside stream capture
+ * looks up that array's device address (cudaGetSymbolAddress) with the device current, so
+ * a context re-created after cudaDeviceReset is picked up; a captured call reuses the
+ * address of the last uncaptured call on the device: make a first call before any capture.  All calls share the array, so calls whose
  * work overlaps on the GPU race on it; nothing in it needs clearing between calls.
  * u, r: device FP64, distinct.  The plan must have been created on the current device. */
 hofem_status hofem_apply_static(hofem_plan_t plan, const double* u, double* r, int nrhs, void* stream);

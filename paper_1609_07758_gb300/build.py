@@ -27,7 +27,9 @@ def nvcc():
 
 # Sources compiled more than once, each time with one macro: the sweep kernels' FP32 and
 # FP64 instantiations (the longest compile) build in parallel with the host helpers.
-PARTS = {"sweep.cu": ["HOFEM_SWEEP_PART=0", "HOFEM_SWEEP_PART=1", "HOFEM_SWEEP_PART=2"]}
+PARTS = {"sweep.cu": ["HOFEM_SWEEP_PART=0", "HOFEM_SWEEP_PART=1", "HOFEM_SWEEP_PART=2"],
+         "sweep_reg.cu": ["HOFEM_REG_PART=0", "HOFEM_REG_PART=1", "HOFEM_REG_PART=2", "HOFEM_REG_PART=3",
+                          "HOFEM_REG_PART=100"]}
 
 
 def sources():
@@ -76,7 +78,7 @@ def build(verbose=False, force=False, lib=None, defines=()):
         if all(os.path.getmtime(d) <= lib_t for d in deps):
             return target
     todo = jobs()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(todo))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(max(os.cpu_count() or 1, 1), 16, len(todo))) as ex:
         results = list(ex.map(lambda j: _compile(j, verbose, defines), todo))
     if verbose:
         for _, log in results:

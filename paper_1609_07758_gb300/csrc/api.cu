@@ -51,6 +51,9 @@ struct DevAxis {
   AxisTables h;
   double *lam64 = nullptr, *mix64 = nullptr, *evec64 = nullptr, *tw64 = nullptr;
   float *lam32 = nullptr, *mix32 = nullptr, *evec32 = nullptr, *tw32 = nullptr;
+  // frequency-fastest copies for the register sweep: mixT[(l n + s)(K-1) + k-1] = G_k[l][s],
+  // lamT[l (K-1) + k-1] = lam[(k-1) n + l] (consecutive threads read consecutive k)
+  float *mixT32 = nullptr, *lamT32 = nullptr;
   int npass = 0, radix[8] = {0};
   int nb = 0;                    // Bluestein length of the K-point DFTs (0: direct passes)
   int mixNP = 0;
@@ -188,6 +191,7 @@ hofem_status upload(const std::vector<double>& src, T** dst, size_t* bytes) {
 void free_axis(DevAxis& a) {
   cudaFree(a.lam64); cudaFree(a.mix64); cudaFree(a.evec64); cudaFree(a.tw64);
   cudaFree(a.lam32); cudaFree(a.mix32); cudaFree(a.evec32); cudaFree(a.tw32);
+  cudaFree(a.mixT32); cudaFree(a.lamT32);
   a = DevAxis{};
 }
 
@@ -364,6 +368,18 @@ TuneKey apply_key(const hofem_plan_s* p, int axis, int mode, long long nrhs) {
   return TuneKey{1, A.h.M, A.h.n, A.h.K, 8, g.inner > 1 ? 1 : 0, mode, nrhs * g.outer_per_rhs * g.inner};
 }
 
+// The register-resident FP32 sweep serves this sweep: an instantiation exists for the
+// axis' (n, K), the formats are FP32/FP64 without FP16 scaling, and HOFEM_SWEEP_REG is not
+// "0" (which forces the general kernel, for comparisons).
+bool use_reg_sweep(const DevAxis& A, bool f64, int in_fmt, int out_fmt, const unsigned long long* in_amax,
+                   const unsigned long long* out_amax, int* W, int* threads, size_t* smem) {
+  if (f64 || in_amax || out_amax) return false;
+  if ((in_fmt != kFmtF64 && in_fmt != kFmtF32) || (out_fmt != kFmtF64 && out_fmt != kFmtF32)) return false;
+  const char* env = getenv("HOFEM_SWEEP_REG");
+  if (env && env[0] == '0') return false;
+  return sweep_reg_shape(A.h.n, A.h.K, W, threads, smem);
+}
+
 hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void* in, int in_fmt, void* out,
                        int out_fmt, bool accumulate, double* norms, long long nrhs, cudaStream_t s,
                        long long lines_override = -1, const unsigned long long* in_amax = nullptr,
@@ -376,14 +392,17 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   const bool strided = g.inner > 1;
   const long long lines = nrhs * g.outer_per_rhs * g.inner;
   int W = 1, J = 1, nwarps = 0;
+  int rthreads = 0;
+  size_t rsmem = 0;
+  const bool reg = use_reg_sweep(A, f64, in_fmt, out_fmt, in_amax, out_amax, &W, &rthreads, &rsmem);
   // the warp-register FFT path is opt-in (HOFEM_WFFT=1): on GB300 it measured slower than
   // the block-wide DIF path (2.5 vs 2.0 ms per sweep at n = 9, K = 1024)
   const char* wf_env = getenv("HOFEM_WFFT");
-  const bool wfft = !f64 && is_pow2(A.h.K) && A.h.K >= 32 && A.h.K <= 1024 && wf_env && wf_env[0] == '1' &&
+  const bool wfft = !reg && !f64 && is_pow2(A.h.K) && A.h.K >= 32 && A.h.K <= 1024 && wf_env && wf_env[0] == '1' &&
                     choose_sweep_wfft(A.h.M, A.h.n, A.h.K, lines, &W, &nwarps);
   const TuneKey key = sweep_key(p, axis, mode, f64, nrhs, lines_override);
   const int NB = sweep_nb(A, tsize);
-  if (wfft) {
+  if (reg || wfft) {
   } else if (g_force_a > 0) {
     W = g_force_a;
     J = g_force_b;
@@ -423,6 +442,8 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   P.norms = norms;
   P.norm_slot = norm_slot;
   P.mix = f64 ? (const void*)A.mix64 : (const void*)A.mix32;
+  P.mixT = A.mixT32;
+  P.lamT = A.lamT32;
   P.mixNP = A.mixNP;
   P.evec = f64 ? (const void*)A.evec64 : (const void*)A.evec32;
   P.tw = f64 ? (const void*)A.tw64 : (const void*)A.tw32;
@@ -470,12 +491,14 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   P.fbuf_complex = wfft ? wfft_fbuf_complex(W, A.h.n, A.h.K, nwarps) : sweep_fbuf_complex(A.h.K, P.nb, J, tsize);
   if (strided) { P.ps = W; P.ws = 1; } else { P.ps = 1; P.ws = A.h.M; }
   P.tile_elems = sweep_tile_elems(A.h.M, W, tsize);
-  P.threads = wfft ? 32 * nwarps : (f64 ? 512 : HOFEM_F32_THREADS);
-  P.smem_bytes = sweep_smem_bytes_fbuf(A.h.M, W, P.fbuf_complex, tsize);
+  P.threads = reg ? rthreads : wfft ? 32 * nwarps : (f64 ? 512 : HOFEM_F32_THREADS);
+  P.smem_bytes = reg ? rsmem : sweep_smem_bytes_fbuf(A.h.M, W, P.fbuf_complex, tsize);
   p->info.lines_per_cta[axis] = W;
   if (P.ntiles <= 0) return HOFEM_OK;
   const int kind = (f64 ? 0 : 3) + (mode == kFwd ? 0 : mode == kFwdScaleInv ? 1 : 2);
-  cudaError_t e = timed_launch(p, kind, s, [&]() { return f64 ? launch_sweep_f64(P, s) : launch_sweep_f32(P, s); });
+  cudaError_t e = timed_launch(p, kind, s, [&]() {
+    return reg ? launch_sweep_reg(P, s) : f64 ? launch_sweep_f64(P, s) : launch_sweep_f32(P, s);
+  });
   if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
   return HOFEM_OK;
 }
@@ -695,7 +718,7 @@ hofem_status device_dot(hofem_plan_s* p, const double* x, const double* y, cudaS
 namespace hofem {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 size_t static_scratch_doubles();
-cudaError_t static_scratch_pointer(double** out);
+cudaError_t static_scratch_pointer(cudaStream_t s, double** out);
 }  // namespace hofem
 
 namespace {
@@ -712,7 +735,7 @@ hofem_status operator_apply_static(hofem_plan_s* p, const double* u, double* out
     return fail(HOFEM_ERR_INVALID_ARG, msg);
   }
   double* base = nullptr;
-  cudaError_t e = static_scratch_pointer(&base);
+  cudaError_t e = static_scratch_pointer(s, &base);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
   double* t[4] = {base, base + cnt, base + 2 * cnt, base + 3 * cnt};
   double sc[3];
@@ -808,6 +831,12 @@ hofem_status tune_plan(hofem_plan_s* p, int nrhs, cudaStream_t s, int* measured)
     int a0, b0;
     if (tuned_lookup(key, &a0, &b0)) continue;
     const DevAxis& A = p->ax[w.axis];
+    {
+      int rw = 0, rt = 0;
+      size_t rs = 0;
+      const unsigned long long* am = (!f64 && p->wfmt == kFmtF16) ? p->amax : nullptr;
+      if (use_reg_sweep(A, f64, w.in_fmt, w.out_fmt, am, am, &rw, &rt, &rs)) continue;   // fixed shape
+    }
     const long long lines = std::get<7>(key);
     const bool strided = std::get<5>(key) == 1;
     double best = 1e30;
@@ -936,6 +965,7 @@ hofem_status hofem_plan_orders(int N, const int* K, const int* ns, const double*
     std::lock_guard<std::mutex> lock(mu);
     if (std::find(done.begin(), done.end(), dev) == done.end()) {
       HOFEM_CUDA(sweep_set_smem_limits(), "cudaFuncSetAttribute(sweep)");
+      HOFEM_CUDA(sweep_reg_set_smem_limits(), "cudaFuncSetAttribute(sweep_reg)");
       HOFEM_CUDA(apply_set_smem_limits(), "cudaFuncSetAttribute(apply)");
       done.push_back(dev);
     }
@@ -1000,6 +1030,17 @@ hofem_status hofem_plan_orders(int N, const int* K, const int* ns, const double*
       a.mixNP = np;
       if ((st = upload(padded, &a.mix64, &tb)) != HOFEM_OK) break;
       if ((st = upload(padded, &a.mix32, &tb)) != HOFEM_OK) break;
+    }
+    {
+      const int na = ns[i], Km = K[i] - 1;
+      std::vector<double> mt((size_t)Km * na * na), lt((size_t)Km * na);
+      for (int k = 0; k < Km; ++k)
+        for (int l = 0; l < na; ++l) {
+          lt[(size_t)l * Km + k] = a.h.lam[(size_t)k * na + l];
+          for (int c = 0; c < na; ++c) mt[((size_t)l * na + c) * Km + k] = a.h.mix[((size_t)k * na + l) * na + c];
+        }
+      if ((st = upload(mt, &a.mixT32, &tb)) != HOFEM_OK) break;
+      if ((st = upload(lt, &a.lamT32, &tb)) != HOFEM_OK) break;
     }
     if ((st = upload(a.h.evec, &a.evec64, &tb)) != HOFEM_OK) break;
     if ((st = upload(a.h.tw, &a.tw64, &tb)) != HOFEM_OK) break;

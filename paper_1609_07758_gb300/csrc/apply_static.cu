@@ -27,14 +27,20 @@ constexpr int kMaxDevices = 64;
 std::mutex g_static_mutex;
 double* g_static_ptr[kMaxDevices] = {nullptr};
 
-// Device address of g_static_scratch on the current device (first call per device: set-up).
-cudaError_t static_scratch_address(double** out) {
+// Device address of g_static_scratch on the current device.  Outside stream capture the
+// address is looked up again on every call, so that a context torn down and re-created
+// (cudaDeviceReset) never leaves a stale cached address; inside capture the address
+// cached by the last uncaptured call on this device is used (set-up happens there).
+cudaError_t static_scratch_address(cudaStream_t s, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (!g_static_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_static_ptr[dev]) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_static_scratch);
     if (e != cudaSuccess) return e;
@@ -48,6 +54,6 @@ cudaError_t static_scratch_address(double** out) {
 
 size_t static_scratch_doubles() { return kStaticScratchDoubles; }
 
-cudaError_t static_scratch_pointer(double** out) { return static_scratch_address(out); }
+cudaError_t static_scratch_pointer(cudaStream_t s, double** out) { return static_scratch_address(s, out); }
 
 }  // namespace hofem

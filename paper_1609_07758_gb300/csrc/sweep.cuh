@@ -56,6 +56,8 @@ struct SweepParams {
   const void* evec;           // (n-1)^2
   const void* tw;             // 2K complex exp(-i pi t / K)
   const void* lam;            // M
+  const float* mixT;          // FP32 (K-1) n n, frequency fastest: [(l n + s)(K-1) + k-1]
+  const float* lamT;          // FP32 (K-1) n, frequency fastest: [l (K-1) + k-1]
   // eigenvalue sums of the other axes for the fused sweep (lines are columns c)
   const void* lamA;           // lam_rest(c) = lamA[c / MB] + lamB[c % MB] (lamB may be null)
   const void* lamB;
@@ -88,6 +90,14 @@ struct SweepParams {
   int threads;
   size_t smem_bytes;
 };
+
+// Register-resident FP32 sweep (sweep_reg.cu) for the element orders and power-of-two K
+// it is instantiated for: lines per CTA, threads and dynamic shared memory of (n, K), or
+// false when there is no instantiation.  Input FP64 or FP32, output FP32 or FP64 (with
+// accumulate and norms); no per-rhs scaling or FP16 prescale.
+bool sweep_reg_shape(int n, int K, int* W, int* threads, size_t* smem);
+cudaError_t sweep_reg_set_smem_limits();
+cudaError_t launch_sweep_reg(const SweepParams& p, cudaStream_t s);
 
 // Launch one sweep; T = float or double work precision.
 cudaError_t launch_sweep_f32(const SweepParams& p, cudaStream_t s);

@@ -1,0 +1,664 @@
+// Register-resident axis sweep (FP32) for element orders and power-of-two K fixed at
+// compile time: the direct (Theorem 2 part 2) and inverse (Theorem 2 part 1) F_n-transforms
+// of W lines of one axis, optionally fused with the eigenvalue-sum division of algorithm (a)
+// (Eq. decomp v 2).  Same line layout, spectral layout and tables as sweep_kernel.
+//
+// DST-I of a job (two real sequences a, b of length K-1 as x_j = a_j + i b_j, x_0 = 0):
+// with X = DFT_K(x) and Z = DFT_K(x_j e^{-i pi j / K}) (the even and odd bins of the
+// 2K-point DFT of x zero-padded),
+//   2 DST(a)_k = -Im D,  2 DST(b)_k = Re D,   D = X_m - X_{K-m}       (k = 2m)
+//                                             D = Z_m - Z_{K-1-m}     (k = 2m + 1).
+// Each K-point DFT (K = 32 L) runs on a group of L lanes with 32 complex values per lane in
+// registers: lane r holds x_{r + L n2} (n2 < 32); a 32-point DFT over n2 with compile-time
+// twiddles, the inter-stage twiddle w_K^{r k2} (w_2K^{r (2 k2 + 1)} for Z), a transpose
+// within the group through shared memory, and 32 / L L-point DFTs leave X_{k2 + 32 k1}
+// (k2 = r + L t) in register t L + k1.  The partner X_{K-m} of every output sits in lane
+// L - r (Z_{K-1-m} in lane L - 1 - r) of the same group at a register fixed at compile
+// time, so the DST outputs come out of one shuffle per value.
+//
+// The pre-combine of the direct transform and the post-combine of the inverse one are
+// gathers from the tile (in the DST loads and in the store), so every job works on its
+// own slots and no phase needs an in-place update.  Each warp holds one job (K = 1024) or
+// 32 / L jobs, each transposing through its own area of shared memory.
+#include <cstdint>
+#include <cstdlib>
+
+#include "sweep.cuh"
+
+#ifndef HOFEM_REG_PART
+#define HOFEM_REG_PART -1
+#endif
+
+namespace hofem {
+#if HOFEM_REG_PART != 100
+namespace {
+
+// cos(2 pi k / 64), k = 0..16
+__host__ __device__ constexpr double cos64_q(int k) {
+  switch (k) {
+    case 0: return 1.0;
+    case 1: return 0.99518472667219688624;
+    case 2: return 0.98078528040323044913;
+    case 3: return 0.95694033573220886494;
+    case 4: return 0.92387953251128675613;
+    case 5: return 0.88192126434835502971;
+    case 6: return 0.83146961230254523708;
+    case 7: return 0.77301045336273696081;
+    case 8: return 0.70710678118654752440;
+    case 9: return 0.63439328416364549822;
+    case 10: return 0.55557023301960222474;
+    case 11: return 0.47139673682599764856;
+    case 12: return 0.38268343236508977173;
+    case 13: return 0.29028467725446236764;
+    case 14: return 0.19509032201612826785;
+    case 15: return 0.09801714032956060199;
+    default: return 0.0;
+  }
+}
+
+__host__ __device__ constexpr double cos64(int k) {
+  k &= 63;
+  return k <= 16 ? cos64_q(k) : k <= 32 ? -cos64_q(32 - k) : k <= 48 ? -cos64_q(k - 32) : cos64_q(64 - k);
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// b exp(-2 pi i e / 64) for an exponent known at compile time
+__device__ __forceinline__ float2 rot64(float2 b, int e) {
+  e &= 63;
+  if (e == 0) return b;
+  if (e == 16) return make_float2(b.y, -b.x);
+  if (e == 32) return make_float2(-b.x, -b.y);
+  if (e == 48) return make_float2(-b.y, b.x);
+  const float c = (float)cos64(e), s = (float)cos64(e - 16);
+  return make_float2(fmaf(b.x, c, b.y * s), fmaf(b.y, c, -b.x * s));
+}
+
+template <int R> __host__ __device__ constexpr int brev(int i) {
+  int o = 0;
+  for (int b = 1; b < R; b <<= 1) {
+    o = (o << 1) | (i & 1);
+    i >>= 1;
+  }
+  return o;
+}
+
+// In-register forward DFT of R = 1..32 points, natural order in and out (radix-2
+// decimation in time after a compile-time bit-reversal of the inputs).
+template <int R> __device__ __forceinline__ void dft(float2 (&v)[R]) {
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int j = brev<R>(i);
+    if (j > i) {
+      const float2 t = v[i];
+      v[i] = v[j];
+      v[j] = t;
+    }
+  }
+#pragma unroll
+  for (int half = 1; half < R; half <<= 1) {
+#pragma unroll
+    for (int s = 0; s < R; s += 2 * half) {
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const float2 a = v[s + k];
+        const float2 b = rot64(v[s + k + half], k * (32 / half));
+        v[s + k] = cadd(a, b);
+        v[s + k + half] = csub(a, b);
+      }
+    }
+  }
+}
+
+// Compile-time shape of one instantiation.
+template <int N_, int LOGK_, int W_, int NW_> struct RegCfg {
+  static constexpr int N = N_, LOGK = LOGK_, W = W_, NW = NW_;
+  static constexpr int K = 1 << LOGK, L = K / 32, T = 32 / L, G = 32 / L;
+  static constexpr int M = N * K - 1;
+  static constexpr int PAIRS = (N - 1) / 2;
+  static constexpr int NJOBS = W * PAIRS + ((N % 2 == 0) ? W : (W + 1) / 2);
+  static constexpr int NT = 32 * NW;
+  // line stride in the tile: >= M and = 32 / W (mod 32) for W | 32, so that the strided
+  // loads (W consecutive lines per row) write distinct banks
+  static constexpr int MSR = (W >= 1 && W <= 32 && (32 % W) == 0) ? (32 / W) % 32 : 1;
+  static constexpr int MS = M + ((MSR - M % 32) % 32 + 32) % 32;
+  static constexpr int WIN = 32 * 33 * 2;          // floats of one warp's transpose area
+  static constexpr int TF = (W * MS + 3) & ~3;
+  static constexpr int SCR = NW * WIN;
+  static constexpr int TWS = 4 * K;                 // floats of the two twiddle tables (K complex each)
+  static constexpr int SAVE = ((W * (N > 1 ? N - 1 : 1)) + 3) & ~3;
+  static constexpr int LR = (W + 3) & ~3;
+  static constexpr size_t SMEM = (size_t)(TF + SCR + TWS + SAVE + LR) * 4 + (size_t)NW * 8;
+  static_assert(LOGK >= 6 && LOGK <= 10, "K = 64 .. 1024");
+  static_assert(NJOBS <= NW * G, "one round of jobs per CTA");
+};
+
+struct RJob {
+  int wa, ca, wb, cb;   // component c of line w; c = 0: nodes; cb < 0: absent
+};
+
+template <class C> __device__ __forceinline__ RJob rjob(int jx) {
+  if (jx < C::W * C::PAIRS) {
+    const int gp = jx / C::W + 1, w = jx % C::W;
+    return RJob{w, gp, w, C::N - gp};
+  }
+  const int r2 = jx - C::W * C::PAIRS;
+  if (C::N % 2 == 0) return RJob{r2, 0, r2, C::N / 2};
+  return RJob{2 * r2, 0, 2 * r2 + 1 < C::W ? 2 * r2 + 1 : 0, 2 * r2 + 1 < C::W ? 0 : -1};
+}
+
+template <class C> __device__ __forceinline__ int slotc(int c) { return c == 0 ? C::N - 1 : c - 1; }
+
+// forward pre-combined sequence of component c of line w at j (1..K-1)
+template <class C> __device__ __forceinline__ float fseq(const float* tile, int w, int c, int j) {
+  const float* t = tile + w * C::MS;
+  if (c == 0) return t[j * C::N - 1];
+  return t[j * C::N + c - 1] + t[(j - 1) * C::N + C::N - c - 1];
+}
+
+// One K-point DFT per lane group on v (see the file comment); Z selects the odd bins.
+// twt: the pass's inter-stage twiddles in shared memory, twt[k2 L + r] = w_K^{r k2} (X) or
+// w_2K^{r (2 k2 + 1)} (Z), so that the lanes of a group read consecutive entries.
+template <class C, bool Z>
+__device__ __forceinline__ void group_fft(float2 (&v)[32], float2* win, int lane, int g, int r,
+                                          const float2* twt) {
+  constexpr int L = C::L;
+  dft<32>(v);
+  if (r != 0) {
+#pragma unroll
+    for (int k2 = Z ? 0 : 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], twt[k2 * L + r]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k2 = 0; k2 < 32; ++k2) win[k2 * 33 + lane] = v[k2];
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < C::T; ++t) {
+    float2 u[L];
+    const int row = (r + L * t) * 33 + g * L;
+#pragma unroll
+    for (int n1 = 0; n1 < L; ++n1) u[n1] = win[row + n1];
+    dft<L>(u);
+#pragma unroll
+    for (int k1 = 0; k1 < L; ++k1) v[t * L + k1] = u[k1];
+  }
+}
+
+__device__ __forceinline__ float2 shfl2(float2 a, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, a.x, src), __shfl_sync(0xffffffffu, a.y, src));
+}
+
+// D_m = X_m - X_{K-m} for m = r + L t + 32 k1, k1 < L / 2 (d index t (L/2) + k1)
+template <class C> __device__ __forceinline__ void extract_x(const float2 (&v)[32], float2 (&d)[16], int g, int r) {
+  constexpr int L = C::L, T = C::T;
+  const int src = g * L + ((L - r) & (L - 1));
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+#pragma unroll
+    for (int k1 = 0; k1 < L / 2; ++k1) {
+      const float2 pv = shfl2(v[(T - 1 - t) * L + (L - 1 - k1)], src);
+      const float2 own = t >= 1 ? v[(T - t) * L + (L - 1 - k1)] : (k1 >= 1 ? v[L - k1] : v[0]);
+      d[t * (L / 2) + k1] = csub(v[t * L + k1], r == 0 ? own : pv);
+    }
+  }
+}
+
+// D_m = Z_m - Z_{K-1-m}
+template <class C> __device__ __forceinline__ void extract_z(const float2 (&v)[32], float2 (&d)[16], int lane) {
+  constexpr int L = C::L, T = C::T;
+  const int src = lane ^ (L - 1);
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+#pragma unroll
+    for (int k1 = 0; k1 < L / 2; ++k1) {
+      const float2 pv = shfl2(v[(T - 1 - t) * L + (L - 1 - k1)], src);
+      d[t * (L / 2) + k1] = csub(v[t * L + k1], pv);
+    }
+  }
+}
+
+// Input x_j (j = r + L n2) of a job: the pre-combined physical sequences (FWD) or the
+// spectral ones (inverse); zero at j = 0 and for groups without a job.
+template <class C, bool FWD>
+__device__ __forceinline__ float2 job_input(const float* tile, const RJob& jb, bool active, int j) {
+  float2 val = make_float2(0.f, 0.f);
+  if (active && j > 0) {
+    if (FWD) {
+      val.x = fseq<C>(tile, jb.wa, jb.ca, j);
+      if (jb.cb >= 0) val.y = fseq<C>(tile, jb.wb, jb.cb, j);
+    } else {
+      val.x = tile[jb.wa * C::MS + (j - 1) * C::N + slotc<C>(jb.ca)];
+      if (jb.cb >= 0) val.y = tile[jb.wb * C::MS + (j - 1) * C::N + slotc<C>(jb.cb)];
+    }
+  }
+  return val;
+}
+
+// All DST jobs of the tile.  FWD: pre-combined physical sequences -> 2 x DST in the
+// spectral slots.  Inverse: spectral sequences -> 2 x DST (D_j) in the same slots.
+// Per job: X from the loaded inputs, its outputs held in registers; the inputs loaded
+// again, times w_64^{n2}, for Z; a barrier (every job's reads of the tile are done); the
+// X outputs stored; Z, whose outputs are stored as they are extracted.  The transposes
+// use the warp's own area of `scr`.
+template <class C, bool FWD>
+__device__ __forceinline__ void dst_jobs(float* tile, float* scr, const float2* twx, const float2* twz) {
+  constexpr int L = C::L, N = C::N;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int g = lane / L, r = lane % L;
+  const int jx = wid * C::G + g;
+  const bool active = jx < C::NJOBS;
+  const RJob jb = rjob<C>(active ? jx : 0);
+  float2* win = reinterpret_cast<float2*>(scr) + wid * (C::WIN / 2);
+  float2 v[32], d[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 32; ++n2) v[n2] = job_input<C, FWD>(tile, jb, active, r + L * n2);
+  group_fft<C, false>(v, win, lane, g, r, twx);
+  extract_x<C>(v, d, g, r);
+#pragma unroll
+  for (int n2 = 0; n2 < 32; ++n2) v[n2] = rot64(job_input<C, FWD>(tile, jb, active, r + L * n2), n2);
+  __syncthreads();   // every job has read its inputs: the tile takes the outputs
+  float* ta = tile + jb.wa * C::MS + slotc<C>(jb.ca);
+  float* tb = jb.cb >= 0 ? tile + jb.wb * C::MS + slotc<C>(jb.cb) : nullptr;
+  if (active) {
+#pragma unroll
+    for (int t = 0; t < C::T; ++t) {
+#pragma unroll
+      for (int k1 = 0; k1 < L / 2; ++k1) {
+        const int m = r + L * t + 32 * k1;
+        const float2 a = d[t * (L / 2) + k1];
+        if (m >= 1) {                                 // k = 2m at block k - 1
+          ta[(2 * m - 1) * N] = -a.y;
+          if (tb) tb[(2 * m - 1) * N] = a.x;
+        }
+      }
+    }
+  }
+  __syncwarp();      // the first transpose's reads are done before the area is rewritten
+  group_fft<C, true>(v, win, lane, g, r, twz);
+  extract_z<C>(v, d, lane);
+  if (active) {
+#pragma unroll
+    for (int t = 0; t < C::T; ++t) {
+#pragma unroll
+      for (int k1 = 0; k1 < L / 2; ++k1) {
+        const int m = r + L * t + 32 * k1;
+        const float2 b = d[t * (L / 2) + k1];
+        ta[(2 * m) * N] = -b.y;                       // k = 2m + 1
+        if (tb) tb[(2 * m) * N] = b.x;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Per-frequency mixing, one thread per frequency k and every line of the tile; the k = 0
+// block by one thread per line.  MODE: kFwd (w = G x / 2K), kInv (x = G^T w / 2) or
+// kFwdScaleInv (both, with the division by lam + rest between them).  G_k is read from the
+// frequency-fastest copy of the table (consecutive threads, consecutive addresses) into
+// registers and applied to the lines one by one.
+template <class C, int MODE>
+__device__ __forceinline__ void mixing(float* tile, float* save, const float* lrest, const SweepParams& P) {
+  constexpr int N = C::N, K = C::K, W = C::W, KM = C::K - 1;
+  const float* __restrict__ mt = P.mixT;
+  const float* __restrict__ lt = P.lamT;
+  const float* __restrict__ lam = (const float*)P.lam;
+  for (int k = 1 + (int)threadIdx.x; k < K; k += C::NT) {
+    const int kk = k - 1, base = kk * N;
+    float G[N][N], lq[N];
+#pragma unroll
+    for (int l = 0; l < N; ++l)
+#pragma unroll
+      for (int s = 0; s < N; ++s) G[l][s] = __ldg(mt + (l * N + s) * KM + kk);
+    if (MODE == kFwdScaleInv) {
+#pragma unroll
+      for (int l = 0; l < N; ++l) lq[l] = __ldg(lt + l * KM + kk);
+    }
+#pragma unroll(W <= 4 ? W : 1)
+    for (int w = 0; w < W; ++w) {
+      float x[N], y[N];
+#pragma unroll
+      for (int s = 0; s < N; ++s) x[s] = tile[w * C::MS + base + s];
+      if (MODE & kFwd) {
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          float acc = 0.f;
+#pragma unroll
+          for (int s = 0; s < N; ++s) acc = fmaf(G[l][s], x[s], acc);
+          y[l] = acc * (0.5f / K);
+        }
+        if (MODE == kFwdScaleInv) {
+          const float rw = lrest[w];
+#pragma unroll
+          for (int l = 0; l < N; ++l) x[l] = y[l] / (lq[l] + rw);
+        }
+      }
+      if (MODE & kInv) {
+#pragma unroll
+        for (int s = 0; s < N; ++s) y[s] = 0.f;
+#pragma unroll
+        for (int l = 0; l < N; ++l)
+#pragma unroll
+          for (int s = 0; s < N; ++s) y[s] = fmaf(G[l][s], x[l], y[s]);
+#pragma unroll
+        for (int s = 0; s < N; ++s) y[s] *= 0.5f;
+      }
+#pragma unroll
+      for (int s = 0; s < N; ++s) tile[w * C::MS + base + s] = y[s];
+    }
+  }
+  if constexpr (N > 1) {
+    constexpr int Mm = N - 1;
+    const float* __restrict__ E = (const float*)P.evec;
+    for (int w = threadIdx.x; w < W; w += C::NT) {
+      const int base = (K - 1) * N;
+      float x[Mm], y[Mm];
+#pragma unroll
+      for (int s = 0; s < Mm; ++s) {
+        x[s] = (MODE & kFwd) ? save[w * Mm + s] : tile[w * C::MS + base + s];
+        y[s] = 0.f;
+      }
+      if (MODE & kFwd) {
+#pragma unroll
+        for (int l = 0; l < Mm; ++l) {
+          float acc = 0.f;
+#pragma unroll
+          for (int s = 0; s < Mm; ++s) acc = fmaf(__ldg(E + l * Mm + s), x[s], acc);
+          y[l] = acc * (1.0f / K);
+        }
+        if (MODE == kFwd) {
+#pragma unroll
+          for (int l = 0; l < Mm; ++l) tile[w * C::MS + base + l] = y[l];
+        } else {
+#pragma unroll
+          for (int l = 0; l < Mm; ++l) {
+            x[l] = y[l] / (__ldg(lam + base + l) + lrest[w]);
+            y[l] = 0.f;
+          }
+        }
+      }
+      if (MODE & kInv) {
+#pragma unroll
+        for (int l = 0; l < Mm; ++l)
+#pragma unroll
+          for (int s = 0; s < Mm; ++s) y[s] = fmaf(__ldg(E + l * Mm + s), x[l], y[s]);
+#pragma unroll
+        for (int s = 0; s < Mm; ++s) save[w * Mm + s] = y[s];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int N, int LOGK, int W, int NW, int MINB>
+__global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepParams P) {
+  using C = RegCfg<N, LOGK, W, NW>;
+  constexpr int M = C::M, MS = C::MS, NT = C::NT, K = C::K;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* tile = reinterpret_cast<float*>(smem_raw);
+  float* scr = tile + C::TF;
+  float2* twx = reinterpret_cast<float2*>(scr + C::SCR);
+  float2* twz = twx + K;
+  float* save = scr + C::SCR + C::TWS;
+  float* lrest = save + C::SAVE;
+  double* red = reinterpret_cast<double*>(lrest + C::LR);
+  const int tid = threadIdx.x;
+
+  const bool contiguous = (P.inner == 1);
+  const long long b = blockIdx.x;
+  const long long o = b / P.tiles_per_outer, tix = b - o * P.tiles_per_outer;
+  const long long l0 = tix * W;
+  const long long nl = contiguous ? P.outer_per_rhs : P.inner;
+  const int wvalid = (int)(nl - l0 < W ? nl - l0 : W);
+  const long long rhs = contiguous ? o : o / P.outer_per_rhs;
+  const long long gbase = contiguous ? (o * P.outer_per_rhs + l0) * (long long)M : o * (long long)M * P.inner + l0;
+  const long long inner = P.inner;
+
+  // ---- load W lines (missing lines read as zeros)
+  constexpr int TOT = W * M, U = 16;
+  if (P.in_fmt == kFmtF64) {
+    const double* __restrict__ in = (const double*)P.in;
+    for (int e0 = tid; e0 < TOT; e0 += U * NT) {
+      float v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * NT;
+        const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
+        v[u] = (e < TOT && w < wvalid) ? (float)__ldg(in + (contiguous ? gbase + e : gbase + p * inner + w)) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * NT;
+        const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
+        if (e < TOT) tile[w * MS + p] = v[u];
+      }
+    }
+  } else {
+    const float* __restrict__ in = (const float*)P.in;
+    for (int e0 = tid; e0 < TOT; e0 += U * NT) {
+      float v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * NT;
+        const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
+        v[u] = (e < TOT && w < wvalid) ? __ldg(in + (contiguous ? gbase + e : gbase + p * inner + w)) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * NT;
+        const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
+        if (e < TOT) tile[w * MS + p] = v[u];
+      }
+    }
+  }
+  {
+    const float2* __restrict__ tw = (const float2*)P.tw;   // exp(-i pi t / K), t < 2K
+    for (int i = tid; i < K; i += NT) {
+      const int k2 = i / C::L, r = i % C::L;
+      twx[i] = __ldg(tw + 2 * r * k2);
+      twz[i] = __ldg(tw + r * (2 * k2 + 1));
+    }
+  }
+  if (P.mode == kFwdScaleInv) {
+    for (int w = tid; w < W; w += NT) {
+      const long long c = l0 + w;
+      float rest = 0.f;
+      if (w < wvalid) {
+        const long long qa = P.lamB ? c / P.MB : c;
+        rest += ((const float*)P.lamA)[qa];
+        if (P.lamB) rest += ((const float*)P.lamB)[c - qa * P.MB];
+      }
+      lrest[w] = (float)P.alpha + rest;
+    }
+  }
+  __syncthreads();
+
+  if (P.mode & kFwd) {
+    // k = 0 sums t_i = sum_j (-P)^{j-1} y_{j-1/2}, component i, one warp per (line, i)
+    if constexpr (N > 1) {
+      const int lane = tid & 31, wid = tid >> 5;
+      for (int item = wid; item < W * (N - 1); item += NW) {
+        const int w = item % W, i = item / W + 1;
+        float acc = 0.f;
+        for (int j = 1 + lane; j <= K; j += 32) {
+          const float v = tile[w * MS + (j - 1) * N + ((j & 1) ? i : N - i) - 1];
+          acc += (j & 1) ? v : -v;
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+        if (lane == 0) save[w * (N - 1) + i - 1] = acc;
+      }
+    }
+    dst_jobs<C, true>(tile, scr, twx, twz);
+    if (P.mode == kFwd) mixing<C, kFwd>(tile, save, lrest, P);
+    else mixing<C, kFwdScaleInv>(tile, save, lrest, P);
+  } else {
+    mixing<C, kInv>(tile, save, lrest, P);
+  }
+  if (P.mode & kInv) dst_jobs<C, false>(tile, scr, twx, twz);
+
+  // ---- store: spectral tile (direct sweep) or the post-combine of the inverse transform,
+  //   v_j = D_j (nodes),  v_{j-1/2,c} = D_{j-1,c} + D_{j,N-c} + (-1)^{j-1} g_{c or N-c}
+  const bool inv = (P.mode & kInv) != 0;
+  const bool want_norm = P.norms != nullptr;
+  float s_d = 0.f;
+  auto value = [&](int w, int p) -> float {
+    const float* t = tile + w * MS;
+    if (!inv) return t[p];
+    const int j = p / N + 1, c = p - (j - 1) * N + 1;
+    if (c == N) return t[p];
+    float v = (j >= 2 ? t[p - N] : 0.f) + (j <= K - 1 ? t[p + N - 2 * c] : 0.f);
+    const float* gs = save + w * (N > 1 ? N - 1 : 1);
+    return v + ((j & 1) ? gs[c - 1] : -gs[N - c - 1]);
+  };
+  if (P.out_fmt == kFmtF64) {
+    double* out = (double*)P.out;
+    for (int e0 = tid; e0 < TOT; e0 += U * NT) {
+      double prev[U];
+      if (P.accumulate) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + u * NT;
+          const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
+          prev[u] = (e < TOT && w < wvalid) ? out[contiguous ? gbase + e : gbase + p * inner + w] : 0.0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * NT;
+        const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
+        if (e < TOT && w < wvalid) {
+          const float tv = value(w, p);
+          const long long ga = contiguous ? gbase + e : gbase + p * inner + w;
+          out[ga] = P.accumulate ? prev[u] + (double)tv : (double)tv;
+          if (want_norm) s_d = fmaf(tv, tv, s_d);
+        }
+      }
+    }
+  } else {
+    float* out = (float*)P.out;
+    for (int e0 = tid; e0 < TOT; e0 += U * NT) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * NT;
+        const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
+        if (e < TOT && w < wvalid) out[contiguous ? gbase + e : gbase + p * inner + w] = value(w, p);
+      }
+    }
+  }
+  if (want_norm) {
+    const int lane = tid & 31, wid = tid >> 5;
+    double sd = (double)s_d;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, s);
+    if (lane == 0) red[wid] = sd;
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0;
+      for (int i = 0; i < NW; ++i) a += red[i];
+      atomicAdd(&P.norms[2 * rhs + P.norm_slot], a);
+    }
+  }
+}
+
+}  // namespace
+#endif
+
+// ---- instantiations: (id, order, log2 K, lines per CTA, warps per CTA, CTAs per SM).
+// The build compiles this file once per instantiation (HOFEM_REG_PART = id) and once for
+// the dispatch table (HOFEM_REG_PART = 100), so the kernels compile in parallel; without the
+// macro one object holds everything.
+#define HOFEM_REG_LIST(X)                                                           \
+  X(0, 9, 10, 2, 9, 1)   /* 2D n = 9, K = 1024 (9215^2 unknowns): 9 jobs, 9 warps */ \
+  X(1, 9, 10, 1, 5, 2)   /* same shape, one line per CTA, two CTAs per SM */        \
+  X(2, 4, 7, 16, 4, 3)   /* 3D n = 4, K = 128 */                                    \
+  X(3, 8, 6, 16, 4, 3)   /* 3D n = 8, K = 64 */
+
+#define HOFEM_REG_DECL(ID, NN, LK, WW, NWW, MB)                      \
+  cudaError_t reg_launch_##ID(const SweepParams& p, cudaStream_t s); \
+  cudaError_t reg_attr_##ID();                                      \
+  size_t reg_smem_##ID();
+HOFEM_REG_LIST(HOFEM_REG_DECL)
+#undef HOFEM_REG_DECL
+
+#define HOFEM_REG_DEF(ID, NN, LK, WW, NWW, MB)                                                           \
+  cudaError_t reg_launch_##ID(const SweepParams& p, cudaStream_t s) {                                   \
+    sweep_reg_kernel<NN, LK, WW, NWW, MB><<<(unsigned)p.ntiles, 32 * NWW, RegCfg<NN, LK, WW, NWW>::SMEM, s>>>(p); \
+    return cudaGetLastError();                                                                          \
+  }                                                                                                     \
+  cudaError_t reg_attr_##ID() {                                                                         \
+    return cudaFuncSetAttribute(sweep_reg_kernel<NN, LK, WW, NWW, MB>,                                  \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
+                                (int)RegCfg<NN, LK, WW, NWW>::SMEM);                                    \
+  }                                                                                                     \
+  size_t reg_smem_##ID() { return RegCfg<NN, LK, WW, NWW>::SMEM; }
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 0
+HOFEM_REG_DEF(0, 9, 10, 2, 9, 1)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 1
+HOFEM_REG_DEF(1, 9, 10, 1, 5, 2)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 2
+HOFEM_REG_DEF(2, 4, 7, 16, 4, 3)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 3
+HOFEM_REG_DEF(3, 8, 6, 16, 4, 3)
+#endif
+
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 100
+namespace {
+
+struct RegEntry {
+  int n, logK, W, nw;
+  cudaError_t (*launch)(const SweepParams&, cudaStream_t);
+  cudaError_t (*attr)();
+  size_t (*smem)();
+};
+
+#define HOFEM_REG_ENTRY(ID, NN, LK, WW, NWW, MB) RegEntry{NN, LK, WW, NWW, reg_launch_##ID, reg_attr_##ID, reg_smem_##ID},
+const RegEntry kRegTable[] = {HOFEM_REG_LIST(HOFEM_REG_ENTRY)};
+#undef HOFEM_REG_ENTRY
+
+// The first instantiation listed for (n, K), or the one with HOFEM_SWEEP_REG_W lines per CTA.
+const RegEntry* reg_entry(int n, int K) {
+  int wantW = 0;
+  if (const char* e = getenv("HOFEM_SWEEP_REG_W")) wantW = atoi(e);
+  const RegEntry* first = nullptr;
+  for (const RegEntry& e : kRegTable) {
+    if (e.n != n || (1 << e.logK) != K) continue;
+    if (!first) first = &e;
+    if (wantW > 0 && e.W == wantW) return &e;
+  }
+  return first;
+}
+
+}  // namespace
+
+bool sweep_reg_shape(int n, int K, int* W, int* threads, size_t* smem) {
+  const RegEntry* e = reg_entry(n, K);
+  if (!e) return false;
+  *W = e->W;
+  *threads = 32 * e->nw;
+  *smem = e->smem();
+  return true;
+}
+
+cudaError_t sweep_reg_set_smem_limits() {
+  for (const RegEntry& e : kRegTable) {
+    cudaError_t r = e.attr();
+    if (r != cudaSuccess) return r;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_sweep_reg(const SweepParams& p, cudaStream_t s) {
+  const RegEntry* e = reg_entry(p.n, p.K);
+  if (!e || e->W != p.W) return cudaErrorInvalidValue;
+  return e->launch(p, s);
+}
+#endif
+
+}  // namespace hofem
