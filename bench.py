@@ -46,8 +46,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the plan-time autotuner (built-in launch shapes)")
-    ap.add_argument("--batch", action="store_true",
-                    help="also time the batched form: 512 uneven 2D problems in one graph launch, refined vs FP64")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched form (512 uneven 2D problems in one graph launch, refined vs FP64)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 3D workloads (n=4 K=128; n=8 K=64 with 16 RHS), refined vs FP64")
     ap.add_argument("--batch-tune", action="store_true",
                     help="autotune every problem of the batch first (84 s for 512 problems; 3%% faster solves)")
     ap.add_argument("--extras", action="store_true",
@@ -255,6 +257,55 @@ def batch_paths(hofem, torch, stream, tune, steps=3):
     return out
 
 
+def config_paths(hofem, torch, stream, steps=2):
+    """The 3D workloads, each refined (library default: corrections until ||delta|| / ||u||
+    <= 1e-12) against the plain FP64 GPU solve on the same seeded input: unknown-RHS per
+    second by CUDA events (plan and first solve outside the time) and the refined solution's
+    relative L2 distance from the FP64 one.  One plan lives at a time (the 16-RHS case holds
+    ~17 GB per FP64 array)."""
+    from paper_1609_07758_gb300 import inputs
+    out = {}
+    cases = [("3d_n4_k128", 4, 128, 1, 3, [("fp32_refined", hofem.HOFEM_FP32_REFINED)]),
+             ("3d_n8_k64_16rhs", 8, 64, 16, 5, [("bf16_refined", hofem.HOFEM_BF16_REFINED),
+                                               ("fp32_refined", hofem.HOFEM_FP32_REFINED)])]
+    for name, n, K, nrhs, seed, dts in cases:
+        M = n * K - 1
+        unknowns = nrhs * M ** 3
+        f = torch.from_numpy(inputs.gaussian_rhs(seed, (nrhs, M, M, M))).cuda()
+        u64 = torch.empty_like(f)
+
+        def run(dtype, u):
+            pl = hofem.Plan(3, [K] * 3, n, [1.0] * 3, dtype)
+            pl.reserve(nrhs)
+            pl.solve(f, u, nrhs, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                pl.solve(f, u, nrhs, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            info = pl.info()
+            pl.close()
+            return e0.elapsed_time(e1) / steps, info.iterations
+
+        ms64, _ = run(hofem.HOFEM_FP64, u64)
+        ent = {"workload": f"3D unit cube, n={n}, K={K} per axis, {M}^3 unknowns x {nrhs} RHS, N(0,1) RHS (seed {seed})",
+               "unknown_rhs": unknowns, "fp64_ms": ms64, "fp64_unknowns_per_s": unknowns / (ms64 / 1e3)}
+        for label, dt in dts:
+            u = torch.empty_like(f)
+            ms, iters = run(dt, u)
+            err = max(float(torch.linalg.vector_norm(u[r] - u64[r]) / torch.linalg.vector_norm(u64[r]))
+                      for r in range(nrhs))
+            ent[label] = {"ms": ms, "unknowns_per_s": unknowns / (ms / 1e3), "corrections": iters,
+                          "max_rel_l2_vs_fp64": err, "speedup_vs_fp64": ms64 / ms}
+            del u
+        out[name] = ent
+        del f, u64
+        torch.cuda.empty_cache()
+    return out
+
+
 def extra_paths(hofem, torch, f, u, stream, args):
     """ms per call of the widened paths at the benchmark size (CUDA events, after warm-up)."""
     K2, X2 = [K_ELEM, K_ELEM], [X_LEN, X_LEN]
@@ -451,7 +502,8 @@ def main():
     extras = None
     if args.extras:
         extras = extra_paths(hofem, torch, f, u, stream, args)
-    batched = batch_paths(hofem, torch, stream, args.batch_tune) if args.batch else None
+    batched = None if args.no_batch else batch_paths(hofem, torch, stream, args.batch_tune)
+    configs = None if args.no_configs else config_paths(hofem, torch, stream)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -462,20 +514,50 @@ def main():
     # algorithmic work per launch (per unknown x unknowns): one operator sweep applies two
     # folded element matrices, 2 (h_even^2 + h_odd^2) flops each per element and line
     fp64_flops_apply = 2 * 2 * (h_even ** 2 + h_odd ** 2) / N_ORDER * UNKNOWNS
-    sweep_bytes = {"sweep_fwd_f32": 12.0, "sweep_fsi_f32": 8.0, "sweep_inv_f32": 20.0,
-                   "sweep_fwd_f64": 16.0, "sweep_fsi_f64": 16.0, "sweep_inv_f64": 16.0}
-    d = kinds[dominant]
-    sec = d["ms_per_launch"] / 1e3
-    if dominant == "apply_f64":
+    # bytes per unknown of each sweep of the FP32-refined path: forward reads FP64, writes FP32;
+    # fused reads and writes FP32; inverse reads FP32 and, in the corrections, the FP64 u it
+    # accumulates into, and writes u (12 B in the first solve of a step, which only writes u)
+    solves = kinds.get("sweep_inv_reg", kinds.get("sweep_inv_f32", {"launches": 0}))["launches"]
+    first = solves / (args.refine_iters + 1) if solves else 0
+    def sweep_bytes(kind, launches):
+        if kind.startswith("sweep_fwd"):
+            return 12.0 * launches * UNKNOWNS
+        if kind.startswith("sweep_fsi"):
+            return 8.0 * launches * UNKNOWNS
+        return (20.0 * (launches - first) + 12.0 * first) * UNKNOWNS
+    # kernel functions: the kinds a function serves, summed
+    functions = {
+        "sweep_reg_kernel (FP32)": [k for k in kinds if k.endswith("_reg")],
+        "sweep_kernel<float>": [k for k in kinds if k.startswith("sweep_") and k.endswith("_f32")],
+        "sweep_kernel<double>": [k for k in kinds if k.startswith("sweep_") and k.endswith("_f64")],
+        "apply_kernel (FP64)": [k for k in kinds if k == "apply_f64"],
+    }
+    fn_ms = {fn: sum(kinds[k]["total_ms"] for k in ks) for fn, ks in functions.items() if ks}
+    dominant_fn = max(fn_ms, key=fn_ms.get)
+
+    def sweep_roof(fn):
+        ks = functions[fn]
+        launches = sum(kinds[k]["launches"] for k in ks)
+        sec = fn_ms[fn] / 1e3 / launches
+        byts = sum(sweep_bytes(k, kinds[k]["launches"]) for k in ks) / launches
+        achieved = byts / sec / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": load_traffic(fn), "kernel": fn, "launches": launches, "ms_per_launch": sec * 1e3,
+                "algorithmic_bytes_per_launch": byts, "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+
+    def apply_roof():
+        d = kinds["apply_f64"]
+        sec = d["ms_per_launch"] / 1e3
         achieved = fp64_flops_apply / sec / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                "frac": achieved / 1.25, "traffic": load_traffic(dominant), "kernel": dominant,
+        return {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s", "frac": achieved / 1.25,
+                "traffic": load_traffic("apply_f64"), "kernel": "apply_kernel (FP64)", "launches": d["launches"],
+                "ms_per_launch": d["ms_per_launch"], "algorithmic_flops_per_launch": fp64_flops_apply,
                 "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe); measured FMA probe 1.20 TFLOP/s"}
-    else:
-        achieved = sweep_bytes[dominant] * UNKNOWNS / sec / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": load_traffic(dominant), "kernel": dominant,
-                "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+
+    roof = apply_roof() if dominant_fn == "apply_kernel (FP64)" else sweep_roof(dominant_fn)
+    sweep_fn = "sweep_reg_kernel (FP32)" if "sweep_reg_kernel (FP32)" in fn_ms else "sweep_kernel<float>"
+    roof_sweep = sweep_roof(sweep_fn) if sweep_fn in fn_ms else None
+    roof_apply = apply_roof() if "apply_f64" in kinds else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -499,6 +581,10 @@ def main():
         "accuracy": {"rel_l2_mixed_vs_fp64": rel_mixed_vs_fp64, "last_rel_update": last_update},
         "verified_default": adaptive,
         "roofline": roof,
+        "roofline_sweep": roof_sweep,
+        "roofline_apply": roof_apply,
+        "sweep_phase_hbm_frac": roof_sweep["frac"] if roof_sweep else None,
+        "kernel_functions_ms": fn_ms,
         "kernels": kinds,
         "cpu_baseline": cpu,
         "e2e": None if args.no_e2e else {"value": job_throughput(UNKNOWNS, world, ms_e2e), "unit": UNIT,
@@ -510,6 +596,7 @@ def main():
         "gpu_launches": launches,
         **({"extras_ms": extras} if extras else {}),
         **({"batched": batched} if batched else {}),
+        **({"configs": configs} if configs else {}),
         "clocks": clock_info,
     }
     if rank == 0:

@@ -120,7 +120,9 @@ typedef struct {
 /* Per-kernel-kind device time, from CUDA events recorded on the launching stream around
  * every kernel while profiling is enabled (see hofem_profile). */
 typedef struct {
-  char name[32];            /* e.g. "sweep_fwd_f32", "apply_f64" */
+  char name[32];            /* "sweep_{fwd,fsi,inv}_{f64,f32}" (general sweep kernel, FP64 or FP32
+                               work), "sweep_{fwd,fsi,inv}_reg" (register-resident FP32 sweep),
+                               "apply_f64" (operator sweep) */
   int launches;
   double total_ms;
 } hofem_kernel_time;

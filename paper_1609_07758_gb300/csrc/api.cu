@@ -54,6 +54,7 @@ struct DevAxis {
   // frequency-fastest copies for the register sweep: mixT[(l n + s)(K-1) + k-1] = G_k[l][s],
   // lamT[l (K-1) + k-1] = lam[(k-1) n + l] (consecutive threads read consecutive k)
   float *mixT32 = nullptr, *lamT32 = nullptr;
+  float* twr32 = nullptr;        // register sweep twiddles (power-of-two K >= 64), see SweepParams::twr
   int npass = 0, radix[8] = {0};
   int nb = 0;                    // Bluestein length of the K-point DFTs (0: direct passes)
   int mixNP = 0;
@@ -107,9 +108,12 @@ struct hofem_plan_s {
 
 namespace {
 
+// kinds 0-5: the general sweep kernel (FP64 / FP32 work), 6: the FP64 operator sweep,
+// 7-9: the register-resident FP32 sweep
 const char* const kKindNames[] = {"sweep_fwd_f64", "sweep_fsi_f64", "sweep_inv_f64", "sweep_fwd_f32",
-                                  "sweep_fsi_f32", "sweep_inv_f32", "apply_f64"};
-constexpr int kNumKinds = 7;
+                                  "sweep_fsi_f32", "sweep_inv_f32", "apply_f64",     "sweep_fwd_reg",
+                                  "sweep_fsi_reg", "sweep_inv_reg"};
+constexpr int kNumKinds = 10;
 
 cudaEvent_t pool_event(hofem_plan_s* p) {
   if (!p->pool.empty()) {
@@ -191,7 +195,7 @@ hofem_status upload(const std::vector<double>& src, T** dst, size_t* bytes) {
 void free_axis(DevAxis& a) {
   cudaFree(a.lam64); cudaFree(a.mix64); cudaFree(a.evec64); cudaFree(a.tw64);
   cudaFree(a.lam32); cudaFree(a.mix32); cudaFree(a.evec32); cudaFree(a.tw32);
-  cudaFree(a.mixT32); cudaFree(a.lamT32);
+  cudaFree(a.mixT32); cudaFree(a.lamT32); cudaFree(a.twr32);
   a = DevAxis{};
 }
 
@@ -444,6 +448,7 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   P.mix = f64 ? (const void*)A.mix64 : (const void*)A.mix32;
   P.mixT = A.mixT32;
   P.lamT = A.lamT32;
+  P.twr = A.twr32;
   P.mixNP = A.mixNP;
   P.evec = f64 ? (const void*)A.evec64 : (const void*)A.evec32;
   P.tw = f64 ? (const void*)A.tw64 : (const void*)A.tw32;
@@ -495,7 +500,7 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   P.smem_bytes = reg ? rsmem : sweep_smem_bytes_fbuf(A.h.M, W, P.fbuf_complex, tsize);
   p->info.lines_per_cta[axis] = W;
   if (P.ntiles <= 0) return HOFEM_OK;
-  const int kind = (f64 ? 0 : 3) + (mode == kFwd ? 0 : mode == kFwdScaleInv ? 1 : 2);
+  const int kind = (reg ? 7 : f64 ? 0 : 3) + (mode == kFwd ? 0 : mode == kFwdScaleInv ? 1 : 2);
   cudaError_t e = timed_launch(p, kind, s, [&]() {
     return reg ? launch_sweep_reg(P, s) : f64 ? launch_sweep_f64(P, s) : launch_sweep_f32(P, s);
   });
@@ -1041,6 +1046,20 @@ hofem_status hofem_plan_orders(int N, const int* K, const int* ns, const double*
         }
       if ((st = upload(mt, &a.mixT32, &tb)) != HOFEM_OK) break;
       if ((st = upload(lt, &a.lamT32, &tb)) != HOFEM_OK) break;
+      if (is_pow2(K[i]) && K[i] >= 64) {
+        // from the DST twiddles exp(-i pi t / K): w_K^{r k2} = tw[2 r k2], w_2K^{r (2k2+1)} = tw[r (2k2+1)]
+        const int L = K[i] / 32;
+        std::vector<double> tr((size_t)4 * K[i]);
+        for (int k2 = 0; k2 < 32; ++k2)
+          for (int r = 0; r < L; ++r) {
+            const size_t ix = (size_t)k2 * L + r, tx = (size_t)2 * r * k2, tz = (size_t)r * (2 * k2 + 1);
+            tr[2 * ix] = a.h.tw[2 * tx];
+            tr[2 * ix + 1] = a.h.tw[2 * tx + 1];
+            tr[2 * (K[i] + ix)] = a.h.tw[2 * tz];
+            tr[2 * (K[i] + ix) + 1] = a.h.tw[2 * tz + 1];
+          }
+        if ((st = upload(tr, &a.twr32, &tb)) != HOFEM_OK) break;
+      }
     }
     if ((st = upload(a.h.evec, &a.evec64, &tb)) != HOFEM_OK) break;
     if ((st = upload(a.h.tw, &a.tw64, &tb)) != HOFEM_OK) break;

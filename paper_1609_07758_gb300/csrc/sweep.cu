@@ -1017,22 +1017,42 @@ __device__ void wfft_dispatch(const Tile<float>& tl, float2* X, int XS, float2* 
   }
 }
 
-// load element i of an array in format fmt, times the power of two sc (applied before
-// any narrowing: FP64 inputs far outside FP32's range keep their bits)
-template <typename T> __device__ __forceinline__ T ldcvt_scaled(const void* p, size_t i, int fmt, double sc) {
-  if (fmt == kFmtF64) return (T)(__ldg((const double*)p + i) * sc);
-  if (fmt == kFmtBF16) return (T)__bfloat162float(__ldg((const __nv_bfloat16*)p + i)) * (T)sc;
-  if (fmt == kFmtF16) return (T)__half2float(__ldg((const __half*)p + i)) * (T)sc;
-  return (T)__ldg((const float*)p + i) * (T)sc;
+// Element i of an array of format FMT (a compile-time constant), times the power of two sc
+// when scaled (applied before any narrowing: FP64 inputs far outside FP32's range keep
+// their bits).
+template <typename T, int FMT> __device__ __forceinline__ T ld_fmt(const void* p, size_t i, bool scaled, double sc) {
+  if constexpr (FMT == kFmtF64) {
+    const double x = __ldg((const double*)p + i);
+    return (T)(scaled ? x * sc : x);
+  } else {
+    float x;
+    if constexpr (FMT == kFmtBF16) x = __bfloat162float(__ldg((const __nv_bfloat16*)p + i));
+    else if constexpr (FMT == kFmtF16) x = __half2float(__ldg((const __half*)p + i));
+    else x = __ldg((const float*)p + i);
+    return scaled ? (T)x * (T)sc : (T)x;
+  }
 }
 
-// load element i of an array in format fmt
-template <typename T> __device__ __forceinline__ T ldcvt(const void* p, size_t i, int fmt) {
-  switch (fmt) {
-    case kFmtF64: return (T)__ldg((const double*)p + i);
-    case kFmtBF16: return (T)__bfloat162float(__ldg((const __nv_bfloat16*)p + i));
-    case kFmtF16: return (T)__half2float(__ldg((const __half*)p + i));
-    default: return (T)__ldg((const float*)p + i);
+// The tile load of a sweep for one input format: the UNR loads of a group are made at
+// clamped valid addresses (an element outside the tile reads element g0) and masked
+// afterwards, so that no branch separates them and all are in flight at once.
+template <typename T, int FMT, typename AddrF, typename ValidF>
+__device__ __forceinline__ void load_tile(T* tile, const void* in, int total, AddrF gaddr, ValidF valid, long long g0,
+                                          bool scaled, double sc) {
+  constexpr int UNR = HOFEM_LOAD_UNROLL;
+  for (int e0 = threadIdx.x; e0 < total; e0 += UNR * blockDim.x) {
+    T v[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const bool ok = e < total && valid(e);
+      v[u] = ld_fmt<T, FMT>(in, (size_t)(ok ? gaddr(e) : g0), scaled, sc);
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < total) tile[e + (e >> TileSwz<T>::v)] = valid(e) ? v[u] : (T)0;
+    }
   }
 }
 
@@ -1086,19 +1106,13 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
   };
   auto valid = [&](int e) -> bool { return contiguous ? (e < wvalid * M) : ((e & (W - 1)) < wvalid); };
   constexpr int UNR = HOFEM_LOAD_UNROLL;
-  for (int e0 = threadIdx.x; e0 < total; e0 += UNR * blockDim.x) {
-    T v[UNR];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const int e = e0 + u * blockDim.x;
-      v[u] = (e < total && valid(e))
-                 ? (P.in_amax ? ldcvt_scaled<T>(P.in, (size_t)gaddr(e), P.in_fmt, in_sc) : ldcvt<T>(P.in, (size_t)gaddr(e), P.in_fmt))
-                 : (T)0;
-    }
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const int e = e0 + u * blockDim.x;
-      if (e < total) tile[e + (e >> TileSwz<T>::v)] = v[u];
+  {
+    const bool scaled = P.in_amax != nullptr;
+    switch (P.in_fmt) {
+      case kFmtF64: load_tile<T, kFmtF64>(tile, P.in, total, gaddr, valid, gbase, scaled, in_sc); break;
+      case kFmtBF16: load_tile<T, kFmtBF16>(tile, P.in, total, gaddr, valid, gbase, scaled, in_sc); break;
+      case kFmtF16: load_tile<T, kFmtF16>(tile, P.in, total, gaddr, valid, gbase, scaled, in_sc); break;
+      default: load_tile<T, kFmtF32>(tile, P.in, total, gaddr, valid, gbase, scaled, in_sc); break;
     }
   }
   if (P.mode == kFwdScaleInv) {
@@ -1178,7 +1192,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
           const int e = e0 + u * blockDim.x;
-          prev[u] = (e < total && valid(e)) ? out[gaddr(e)] : 0.0;
+          prev[u] = out[(e < total && valid(e)) ? gaddr(e) : gbase];   // clamped: no branch
         }
       }
 #pragma unroll

@@ -58,6 +58,8 @@ struct SweepParams {
   const void* lam;            // M
   const float* mixT;          // FP32 (K-1) n n, frequency fastest: [(l n + s)(K-1) + k-1]
   const float* lamT;          // FP32 (K-1) n, frequency fastest: [l (K-1) + k-1]
+  const float* twr;           // FP32 complex, K = 32 L a power of two >= 64: K entries
+                              // w_K^{r k2} at [k2 L + r], then K entries w_2K^{r (2 k2 + 1)}
   // eigenvalue sums of the other axes for the fused sweep (lines are columns c)
   const void* lamA;           // lam_rest(c) = lamA[c / MB] + lamB[c % MB] (lamB may be null)
   const void* lamB;

@@ -19,7 +19,8 @@
 // The pre-combine of the direct transform and the post-combine of the inverse one are
 // gathers from the tile (in the DST loads and in the store), so every job works on its
 // own slots and no phase needs an in-place update.  Each warp holds one job (K = 1024) or
-// 32 / L jobs, each transposing through its own area of shared memory.
+// 32 / L jobs at a time, transposing through its own area of shared memory; a CTA runs its
+// jobs in rounds of one per lane group.
 #include <cstdint>
 #include <cstdlib>
 
@@ -78,6 +79,15 @@ __device__ __forceinline__ float2 rot64(float2 b, int e) {
   return make_float2(fmaf(b.x, c, b.y * s), fmaf(b.y, c, -b.x * s));
 }
 
+// 4-byte asynchronous global -> shared copy; src_bytes = 0 writes a zero (nothing is read)
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <int R> __host__ __device__ constexpr int brev(int i) {
   int o = 0;
   for (int b = 1; b < R; b <<= 1) {
@@ -129,12 +139,11 @@ template <int N_, int LOGK_, int W_, int NW_> struct RegCfg {
   static constexpr int WIN = 32 * 33 * 2;          // floats of one warp's transpose area
   static constexpr int TF = (W * MS + 3) & ~3;
   static constexpr int SCR = NW * WIN;
-  static constexpr int TWS = 4 * K;                 // floats of the two twiddle tables (K complex each)
+  static constexpr int ROUNDS = (NJOBS + NW * G - 1) / (NW * G);   // job rounds per CTA
   static constexpr int SAVE = ((W * (N > 1 ? N - 1 : 1)) + 3) & ~3;
   static constexpr int LR = (W + 3) & ~3;
-  static constexpr size_t SMEM = (size_t)(TF + SCR + TWS + SAVE + LR) * 4 + (size_t)NW * 8;
+  static constexpr size_t SMEM = (size_t)(TF + SCR + SAVE + LR) * 4 + (size_t)NW * 8;
   static_assert(LOGK >= 6 && LOGK <= 10, "K = 64 .. 1024");
-  static_assert(NJOBS <= NW * G, "one round of jobs per CTA");
 };
 
 struct RJob {
@@ -153,16 +162,19 @@ template <class C> __device__ __forceinline__ RJob rjob(int jx) {
 
 template <class C> __device__ __forceinline__ int slotc(int c) { return c == 0 ? C::N - 1 : c - 1; }
 
-// forward pre-combined sequence of component c of line w at j (1..K-1)
+// forward pre-combined sequence of component c of line w at j (1..K-1); both reads are
+// unconditional (for the nodes, c = 0, the second index is the first one), so that the
+// unrolled loads of a job issue back to back
 template <class C> __device__ __forceinline__ float fseq(const float* tile, int w, int c, int j) {
   const float* t = tile + w * C::MS;
-  if (c == 0) return t[j * C::N - 1];
-  return t[j * C::N + c - 1] + t[(j - 1) * C::N + C::N - c - 1];
+  const float v1 = t[c == 0 ? j * C::N - 1 : j * C::N + c - 1];
+  const float v2 = t[(j - 1) * C::N + C::N - c - 1];
+  return c == 0 ? v1 : v1 + v2;
 }
 
-// One K-point DFT per lane group on v (see the file comment); Z selects the odd bins.
-// twt: the pass's inter-stage twiddles in shared memory, twt[k2 L + r] = w_K^{r k2} (X) or
-// w_2K^{r (2 k2 + 1)} (Z), so that the lanes of a group read consecutive entries.
+// twt: the pass's inter-stage twiddles, twt[k2 L + r] = w_K^{r k2} (X) or w_2K^{r (2 k2 + 1)}
+// (Z), a K-entry table in global memory (L1-resident) laid out so that the lanes of a group
+// read consecutive entries.
 template <class C, bool Z>
 __device__ __forceinline__ void group_fft(float2 (&v)[32], float2* win, int lane, int g, int r,
                                           const float2* twt) {
@@ -170,7 +182,7 @@ __device__ __forceinline__ void group_fft(float2 (&v)[32], float2* win, int lane
   dft<32>(v);
   if (r != 0) {
 #pragma unroll
-    for (int k2 = Z ? 0 : 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], twt[k2 * L + r]);
+    for (int k2 = Z ? 0 : 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], __ldg(twt + k2 * L + r));
   }
   __syncwarp();
 #pragma unroll
@@ -222,20 +234,22 @@ template <class C> __device__ __forceinline__ void extract_z(const float2 (&v)[3
 }
 
 // Input x_j (j = r + L n2) of a job: the pre-combined physical sequences (FWD) or the
-// spectral ones (inverse); zero at j = 0 and for groups without a job.
+// spectral ones (inverse); zero at j = 0 and for groups without a job.  Reads are made at
+// clamped, valid indices and masked afterwards (no branch around a load).
 template <class C, bool FWD>
 __device__ __forceinline__ float2 job_input(const float* tile, const RJob& jb, bool active, int j) {
-  float2 val = make_float2(0.f, 0.f);
-  if (active && j > 0) {
-    if (FWD) {
-      val.x = fseq<C>(tile, jb.wa, jb.ca, j);
-      if (jb.cb >= 0) val.y = fseq<C>(tile, jb.wb, jb.cb, j);
-    } else {
-      val.x = tile[jb.wa * C::MS + (j - 1) * C::N + slotc<C>(jb.ca)];
-      if (jb.cb >= 0) val.y = tile[jb.wb * C::MS + (j - 1) * C::N + slotc<C>(jb.cb)];
-    }
+  const int jj = j > 0 ? j : 1;
+  const bool ok = active && j > 0, okb = ok && jb.cb >= 0;
+  const int cb = jb.cb >= 0 ? jb.cb : jb.ca;
+  float a, b;
+  if (FWD) {
+    a = fseq<C>(tile, jb.wa, jb.ca, jj);
+    b = fseq<C>(tile, jb.wb, cb, jj);
+  } else {
+    a = tile[jb.wa * C::MS + (jj - 1) * C::N + slotc<C>(jb.ca)];
+    b = tile[jb.wb * C::MS + (jj - 1) * C::N + slotc<C>(cb)];
   }
-  return val;
+  return make_float2(ok ? a : 0.f, okb ? b : 0.f);
 }
 
 // All DST jobs of the tile.  FWD: pre-combined physical sequences -> 2 x DST in the
@@ -245,50 +259,56 @@ __device__ __forceinline__ float2 job_input(const float* tile, const RJob& jb, b
 // X outputs stored; Z, whose outputs are stored as they are extracted.  The transposes
 // use the warp's own area of `scr`.
 template <class C, bool FWD>
-__device__ __forceinline__ void dst_jobs(float* tile, float* scr, const float2* twx, const float2* twz) {
+__device__ __forceinline__ void dst_jobs(float* tile, float* scr, const float2* __restrict__ twx,
+                                         const float2* __restrict__ twz) {
   constexpr int L = C::L, N = C::N;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int g = lane / L, r = lane % L;
-  const int jx = wid * C::G + g;
-  const bool active = jx < C::NJOBS;
-  const RJob jb = rjob<C>(active ? jx : 0);
   float2* win = reinterpret_cast<float2*>(scr) + wid * (C::WIN / 2);
-  float2 v[32], d[16];
+#pragma unroll 1
+  for (int round = 0; round < C::ROUNDS; ++round) {
+    // jobs touch disjoint slots of the tile, so a later round's inputs are intact
+    const int jx = (round * C::NW + wid) * C::G + g;
+    const bool active = jx < C::NJOBS;
+    const RJob jb = rjob<C>(active ? jx : 0);
+    float2 v[32], d[16];
 #pragma unroll
-  for (int n2 = 0; n2 < 32; ++n2) v[n2] = job_input<C, FWD>(tile, jb, active, r + L * n2);
-  group_fft<C, false>(v, win, lane, g, r, twx);
-  extract_x<C>(v, d, g, r);
+    for (int n2 = 0; n2 < 32; ++n2) v[n2] = job_input<C, FWD>(tile, jb, active, r + L * n2);
+    __syncwarp();    // the previous round's reads of the transpose area are done
+    group_fft<C, false>(v, win, lane, g, r, twx);
+    extract_x<C>(v, d, g, r);
 #pragma unroll
-  for (int n2 = 0; n2 < 32; ++n2) v[n2] = rot64(job_input<C, FWD>(tile, jb, active, r + L * n2), n2);
-  __syncthreads();   // every job has read its inputs: the tile takes the outputs
-  float* ta = tile + jb.wa * C::MS + slotc<C>(jb.ca);
-  float* tb = jb.cb >= 0 ? tile + jb.wb * C::MS + slotc<C>(jb.cb) : nullptr;
-  if (active) {
+    for (int n2 = 0; n2 < 32; ++n2) v[n2] = rot64(job_input<C, FWD>(tile, jb, active, r + L * n2), n2);
+    __syncthreads();   // every job of this round has read its inputs
+    float* ta = tile + jb.wa * C::MS + slotc<C>(jb.ca);
+    float* tb = jb.cb >= 0 ? tile + jb.wb * C::MS + slotc<C>(jb.cb) : nullptr;
+    if (active) {
 #pragma unroll
-    for (int t = 0; t < C::T; ++t) {
+      for (int t = 0; t < C::T; ++t) {
 #pragma unroll
-      for (int k1 = 0; k1 < L / 2; ++k1) {
-        const int m = r + L * t + 32 * k1;
-        const float2 a = d[t * (L / 2) + k1];
-        if (m >= 1) {                                 // k = 2m at block k - 1
-          ta[(2 * m - 1) * N] = -a.y;
-          if (tb) tb[(2 * m - 1) * N] = a.x;
+        for (int k1 = 0; k1 < L / 2; ++k1) {
+          const int m = r + L * t + 32 * k1;
+          const float2 a = d[t * (L / 2) + k1];
+          if (m >= 1) {                               // k = 2m at block k - 1
+            ta[(2 * m - 1) * N] = -a.y;
+            if (tb) tb[(2 * m - 1) * N] = a.x;
+          }
         }
       }
     }
-  }
-  __syncwarp();      // the first transpose's reads are done before the area is rewritten
-  group_fft<C, true>(v, win, lane, g, r, twz);
-  extract_z<C>(v, d, lane);
-  if (active) {
+    __syncwarp();    // the first transpose's reads are done before the area is rewritten
+    group_fft<C, true>(v, win, lane, g, r, twz);
+    extract_z<C>(v, d, lane);
+    if (active) {
 #pragma unroll
-    for (int t = 0; t < C::T; ++t) {
+      for (int t = 0; t < C::T; ++t) {
 #pragma unroll
-      for (int k1 = 0; k1 < L / 2; ++k1) {
-        const int m = r + L * t + 32 * k1;
-        const float2 b = d[t * (L / 2) + k1];
-        ta[(2 * m) * N] = -b.y;                       // k = 2m + 1
-        if (tb) tb[(2 * m) * N] = b.x;
+        for (int k1 = 0; k1 < L / 2; ++k1) {
+          const int m = r + L * t + 32 * k1;
+          const float2 b = d[t * (L / 2) + k1];
+          ta[(2 * m) * N] = -b.y;                     // k = 2m + 1
+          if (tb) tb[(2 * m) * N] = b.x;
+        }
       }
     }
   }
@@ -333,7 +353,7 @@ __device__ __forceinline__ void mixing(float* tile, float* save, const float* lr
         if (MODE == kFwdScaleInv) {
           const float rw = lrest[w];
 #pragma unroll
-          for (int l = 0; l < N; ++l) x[l] = y[l] / (lq[l] + rw);
+          for (int l = 0; l < N; ++l) x[l] = y[l] * __frcp_rn(lq[l] + rw);
         }
       }
       if (MODE & kInv) {
@@ -400,9 +420,9 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* tile = reinterpret_cast<float*>(smem_raw);
   float* scr = tile + C::TF;
-  float2* twx = reinterpret_cast<float2*>(scr + C::SCR);
-  float2* twz = twx + K;
-  float* save = scr + C::SCR + C::TWS;
+  float* save = scr + C::SCR;
+  const float2* twx = (const float2*)P.twr;
+  const float2* twz = twx + K;
   float* lrest = save + C::SAVE;
   double* red = reinterpret_cast<double*>(lrest + C::LR);
   const int tid = threadIdx.x;
@@ -417,50 +437,46 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
   const long long gbase = contiguous ? (o * P.outer_per_rhs + l0) * (long long)M : o * (long long)M * P.inner + l0;
   const long long inner = P.inner;
 
-  // ---- load W lines (missing lines read as zeros)
-  constexpr int TOT = W * M, U = 16;
+  // ---- load W lines (missing lines read as zeros).  Element e is (line w, position p):
+  // e = w M + p (contiguous lines) or e = p W + w (strided columns).  The loads of an
+  // unrolled group are unconditional (out-of-range elements read the tile's first element)
+  // so that they are all in flight at once.
+  constexpr int TOT = W * M, U = 16, UL = 32;
+  auto decode = [&](int e, int& w, int& p) {
+    if (contiguous) { w = e / M; p = e - w * M; }
+    else { w = e % W; p = e / W; }
+  };
+  auto gaddr = [&](int w, int p) -> long long { return contiguous ? gbase + (long long)w * M + p : gbase + p * inner + w; };
   if (P.in_fmt == kFmtF64) {
+    // FP64 input (narrowed on the way): UL loads per thread in flight in registers
     const double* __restrict__ in = (const double*)P.in;
-    for (int e0 = tid; e0 < TOT; e0 += U * NT) {
-      float v[U];
+    for (int e0 = tid; e0 < TOT; e0 += UL * NT) {
+      double v[UL];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int e = e0 + u * NT;
-        const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
-        v[u] = (e < TOT && w < wvalid) ? (float)__ldg(in + (contiguous ? gbase + e : gbase + p * inner + w)) : 0.f;
+      for (int u = 0; u < UL; ++u) {
+        int w, p;
+        decode(e0 + u * NT, w, p);
+        const bool ok = e0 + u * NT < TOT && w < wvalid;
+        v[u] = __ldg(in + (ok ? gaddr(w, p) : gbase));
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int e = e0 + u * NT;
-        const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
-        if (e < TOT) tile[w * MS + p] = v[u];
+      for (int u = 0; u < UL; ++u) {
+        int w, p;
+        decode(e0 + u * NT, w, p);
+        if (e0 + u * NT < TOT) tile[w * MS + p] = w < wvalid ? (float)v[u] : 0.f;
       }
     }
   } else {
+    // FP32 input: asynchronous 4-byte copies straight into the tile (zero-filled for the
+    // missing lines), the whole tile in flight at once
     const float* __restrict__ in = (const float*)P.in;
-    for (int e0 = tid; e0 < TOT; e0 += U * NT) {
-      float v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int e = e0 + u * NT;
-        const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
-        v[u] = (e < TOT && w < wvalid) ? __ldg(in + (contiguous ? gbase + e : gbase + p * inner + w)) : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int e = e0 + u * NT;
-        const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
-        if (e < TOT) tile[w * MS + p] = v[u];
-      }
+    for (int e = tid; e < TOT; e += NT) {
+      int w, p;
+      decode(e, w, p);
+      const bool ok = w < wvalid;
+      cp_async4(tile + w * MS + p, in + (ok ? gaddr(w, p) : gbase), ok ? 4 : 0);
     }
-  }
-  {
-    const float2* __restrict__ tw = (const float2*)P.tw;   // exp(-i pi t / K), t < 2K
-    for (int i = tid; i < K; i += NT) {
-      const int k2 = i / C::L, r = i % C::L;
-      twx[i] = __ldg(tw + 2 * r * k2);
-      twz[i] = __ldg(tw + r * (2 * k2 + 1));
-    }
+    cp_async_wait_all();
   }
   if (P.mode == kFwdScaleInv) {
     for (int w = tid; w < W; w += NT) {
@@ -509,10 +525,14 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
     const float* t = tile + w * MS;
     if (!inv) return t[p];
     const int j = p / N + 1, c = p - (j - 1) * N + 1;
-    if (c == N) return t[p];
-    float v = (j >= 2 ? t[p - N] : 0.f) + (j <= K - 1 ? t[p + N - 2 * c] : 0.f);
+    if (N == 1) return t[p];
+    // clamped reads, masked: D_{j-1, c} (j >= 2), D_{j, N-c} (j <= K-1), g (c < N)
+    const int cc = c < N ? c : 1;
+    const float d0 = t[j >= 2 ? p - N : p], d1 = t[j <= K - 1 ? p + N - 2 * cc : p];
     const float* gs = save + w * (N > 1 ? N - 1 : 1);
-    return v + ((j & 1) ? gs[c - 1] : -gs[N - c - 1]);
+    const float ga = gs[cc - 1], gb = gs[N - cc - 1];
+    const float v = (j >= 2 ? d0 : 0.f) + (j <= K - 1 ? d1 : 0.f) + ((j & 1) ? ga : -gb);
+    return c == N ? t[p] : v;
   };
   if (P.out_fmt == kFmtF64) {
     double* out = (double*)P.out;
@@ -521,19 +541,19 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
       if (P.accumulate) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const int e = e0 + u * NT;
-          const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
-          prev[u] = (e < TOT && w < wvalid) ? out[contiguous ? gbase + e : gbase + p * inner + w] : 0.0;
+          int w, p;
+          decode(e0 + u * NT, w, p);
+          const bool ok = e0 + u * NT < TOT && w < wvalid;
+          prev[u] = out[ok ? gaddr(w, p) : gbase];
         }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int e = e0 + u * NT;
-        const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
-        if (e < TOT && w < wvalid) {
+        int w, p;
+        decode(e0 + u * NT, w, p);
+        if (e0 + u * NT < TOT && w < wvalid) {
           const float tv = value(w, p);
-          const long long ga = contiguous ? gbase + e : gbase + p * inner + w;
-          out[ga] = P.accumulate ? prev[u] + (double)tv : (double)tv;
+          out[gaddr(w, p)] = P.accumulate ? prev[u] + (double)tv : (double)tv;
           if (want_norm) s_d = fmaf(tv, tv, s_d);
         }
       }
@@ -543,9 +563,9 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
     for (int e0 = tid; e0 < TOT; e0 += U * NT) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int e = e0 + u * NT;
-        const int w = contiguous ? e / M : e % W, p = contiguous ? e - (e / M) * M : e / W;
-        if (e < TOT && w < wvalid) out[contiguous ? gbase + e : gbase + p * inner + w] = value(w, p);
+        int w, p;
+        decode(e0 + u * NT, w, p);
+        if (e0 + u * NT < TOT && w < wvalid) out[gaddr(w, p)] = value(w, p);
       }
     }
   }
@@ -571,11 +591,12 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
 // The build compiles this file once per instantiation (HOFEM_REG_PART = id) and once for
 // the dispatch table (HOFEM_REG_PART = 100), so the kernels compile in parallel; without the
 // macro one object holds everything.
-#define HOFEM_REG_LIST(X)                                                           \
-  X(0, 9, 10, 2, 9, 1)   /* 2D n = 9, K = 1024 (9215^2 unknowns): 9 jobs, 9 warps */ \
-  X(1, 9, 10, 1, 5, 2)   /* same shape, one line per CTA, two CTAs per SM */        \
-  X(2, 4, 7, 16, 4, 3)   /* 3D n = 4, K = 128 */                                    \
-  X(3, 8, 6, 16, 4, 3)   /* 3D n = 8, K = 64 */
+#define HOFEM_REG_LIST(X)                                                               \
+  X(0, 9, 10, 4, 9, 1)   /* 2D n = 9, K = 1024 (9215^2 unknowns): 18 jobs, 2 rounds of 9 */ \
+  X(1, 9, 10, 1, 5, 2)   /* same shape, one line per CTA, two CTAs per SM */            \
+  X(2, 9, 10, 2, 9, 1)   /* same shape, two lines per CTA */                            \
+  X(3, 4, 7, 16, 4, 3)   /* 3D n = 4, K = 128 */                                        \
+  X(4, 8, 6, 16, 4, 3)   /* 3D n = 8, K = 64 */
 
 #define HOFEM_REG_DECL(ID, NN, LK, WW, NWW, MB)                      \
   cudaError_t reg_launch_##ID(const SweepParams& p, cudaStream_t s); \
@@ -596,16 +617,19 @@ HOFEM_REG_LIST(HOFEM_REG_DECL)
   }                                                                                                     \
   size_t reg_smem_##ID() { return RegCfg<NN, LK, WW, NWW>::SMEM; }
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 0
-HOFEM_REG_DEF(0, 9, 10, 2, 9, 1)
+HOFEM_REG_DEF(0, 9, 10, 4, 9, 1)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 1
 HOFEM_REG_DEF(1, 9, 10, 1, 5, 2)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 2
-HOFEM_REG_DEF(2, 4, 7, 16, 4, 3)
+HOFEM_REG_DEF(2, 9, 10, 2, 9, 1)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 3
-HOFEM_REG_DEF(3, 8, 6, 16, 4, 3)
+HOFEM_REG_DEF(3, 4, 7, 16, 4, 3)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 4
+HOFEM_REG_DEF(4, 8, 6, 16, 4, 3)
 #endif
 
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 100

@@ -53,7 +53,8 @@ def transforms(plan, y, c, lines, M):
     return fwd, out.cpu().numpy()
 
 
-@pytest.mark.parametrize("n,K,lines,W", [(9, 1024, 5, 2), (9, 1024, 3, 1), (4, 128, 37, 16), (8, 64, 21, 16)])
+@pytest.mark.parametrize("n,K,lines,W", [(9, 1024, 5, 4), (9, 1024, 5, 2), (9, 1024, 3, 1), (4, 128, 37, 16),
+                                         (8, 64, 21, 16)])
 def test_register_sweep_transforms_match_oracle(monkeypatch, n, K, lines, W):
     monkeypatch.setenv("HOFEM_SWEEP_REG_W", str(W))
     X = 1.3
