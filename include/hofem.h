@@ -178,6 +178,17 @@ hofem_status hofem_quadrature_points(hofem_plan_t plan, int axis, double* x);
  * Asynchronous on stream; fq != fh. */
 hofem_status hofem_load(hofem_plan_t plan, const double* fq, double* fh, int nrhs, void* stream);
 
+/* Inhomogeneous Dirichlet data u = b on the boundary (the remark after Eq. bvp glob 2 in
+ * Sect. 2 par. 4: the problem reduces to Eq. bvp glob 2 with a modified f^h):
+ *   f <- f - (L^ vb)|interior,  L^ = sum_i 4 h_i^-2 A^_i (x) prod_{m != i} C^_m + alpha prod C^_m,
+ * A^_i, C^_i the 1D matrices of axis i with its two boundary nodes kept (same local A, C).
+ * vb: device FP64 (nrhs, M_1 + 2, .., M_N + 2), the full grid with the boundary nodes at index
+ * 0 and M_i + 1 of every axis (interior dof p at p + 1); only its boundary entries are read
+ * (values of b at the boundary Lagrange points, or any other boundary coefficients).
+ * f: device FP64 (nrhs, M_1..M_N), updated in place (e.g. the f^h of hofem_load); then
+ * hofem_solve gives the interior values of the solution.  Asynchronous on stream; vb != f. */
+hofem_status hofem_lift_dirichlet(hofem_plan_t plan, const double* vb, double* f, int nrhs, void* stream);
+
 /* Algorithm (b) of Sect. 2 par. 4 in FP64: the direct F_n-transforms along x_2..x_N, then
  * for every mode of those axes the banded SPD system (4 h_1^-2 A_1 + sigma C_1) v = f
  * along x_1 (sigma = the mode's eigenvalue sum + alpha), solved by static condensation of

@@ -24,7 +24,7 @@ EXPORTED = (
     "hofem_destroy", "hofem_status_string", "hofem_last_error", "hofem_profile", "hofem_get_profile",
     "hofem_apply_static", "hofem_autotune", "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve",
     "hofem_batch_get_info", "hofem_batch_get_plan", "hofem_batch_destroy", "hofem_quadrature_points",
-    "hofem_load", "hofem_mass", "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders",
+    "hofem_load", "hofem_lift_dirichlet", "hofem_mass", "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders",
     "hofem_apply_varcoef", "hofem_pcg",
 )
 
@@ -102,6 +102,7 @@ def load_library():
     lib.hofem_autotune.argtypes = [P, I, V]
     lib.hofem_quadrature_points.argtypes = [P, I, ctypes.POINTER(D)]
     lib.hofem_load.argtypes = [P, V, V, I, V]
+    lib.hofem_lift_dirichlet.argtypes = [P, V, V, I, V]
     lib.hofem_mass.argtypes = [P, V, V, I, V]
     lib.hofem_solve_banded.argtypes = [P, V, V, I, V]
     lib.hofem_apply_varcoef.argtypes = [P, V, V, V, V]
@@ -118,7 +119,7 @@ def load_library():
                  "hofem_residual", "hofem_transform1d", "hofem_get_eigen", "hofem_get_info",
                  "hofem_profile", "hofem_get_profile", "hofem_apply_static", "hofem_autotune",
                  "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve", "hofem_batch_get_info",
-                 "hofem_batch_get_plan", "hofem_quadrature_points", "hofem_load", "hofem_mass",
+                 "hofem_batch_get_plan", "hofem_quadrature_points", "hofem_load", "hofem_lift_dirichlet", "hofem_mass",
                  "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders", "hofem_apply_varcoef",
                  "hofem_pcg"):
         getattr(lib, name).restype = I
@@ -324,6 +325,12 @@ class Plan:
     def load(self, fq, fh, nrhs, stream=None):
         """fh = f^h from samples fq of f at the tensor product of the quadrature points."""
         _check(load_library().hofem_load(self.handle, _ptr(fq), _ptr(fh), int(nrhs), _stream(stream)), "hofem_load")
+
+    def lift_dirichlet(self, vb, f, nrhs, stream=None):
+        """f -= (full-space operator, interior rows x boundary columns) vb: the Dirichlet
+        data vb, given on the full grid (nrhs, M_1 + 2, ..), moved into the right-hand side."""
+        _check(load_library().hofem_lift_dirichlet(self.handle, _ptr(vb), _ptr(f), int(nrhs), _stream(stream)),
+               "hofem_lift_dirichlet")
 
     def profile(self, enable):
         hofem_profile(self.handle, enable)

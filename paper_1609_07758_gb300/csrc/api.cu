@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "banded.cuh"
+#include "dirichlet.cuh"
 #include "varcoef.cuh"
 #include "load.cuh"
 #include "residual.cuh"
@@ -1145,6 +1146,36 @@ hofem_status hofem_quadrature_points(hofem_plan_t p, int axis, double* x) {
   const double h = p->X[axis] / K;
   for (int e = 0; e < K; ++e)
     for (int g = 0; g < G; ++g) x[(size_t)e * G + g] = e * h + (p->load_xi[axis][g] + 1.0) * h / 2.0;
+  return HOFEM_OK;
+}
+
+hofem_status hofem_lift_dirichlet(hofem_plan_t p, const double* vb, double* f, int nrhs, void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (!vb || !f || nrhs < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or nrhs");
+  if ((const void*)vb == (const void*)f) return fail(HOFEM_ERR_INVALID_ARG, "vb and f must differ");
+  LiftParams L{};
+  L.vb = vb;
+  L.f = f;
+  L.N = p->N;
+  L.nrhs = nrhs;
+  L.alpha = p->alpha;
+  for (int i = 0; i < p->N; ++i) {
+    const AxisTables& h = p->ax[i].h;
+    L.n[i] = h.n;
+    L.M[i] = p->M[i];
+    L.P[i] = p->M[i] + 2;
+    L.coef[i] = 4.0 * (double)p->K[i] * (double)p->K[i] / (p->X[i] * p->X[i]);
+    const int m1 = h.n + 1;
+    if ((int)h.Aloc.size() != m1 * m1 || (int)h.Cloc.size() != m1 * m1)
+      return fail(HOFEM_ERR_UNSUPPORTED, "plan has no local element matrices");
+    for (int k = 0; k < m1 * m1; ++k) {
+      L.A[i][k] = h.Aloc[k];
+      L.C[i][k] = h.Cloc[k];
+    }
+  }
+  cudaError_t e = launch_lift(L, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lift launch");
+  ++p->info.kernel_launches;
   return HOFEM_OK;
 }
 

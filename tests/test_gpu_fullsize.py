@@ -183,3 +183,34 @@ def test_batched_512_problems_refined():
         err = rel_l2(ud[i].cpu().numpy(), ref)
         print(f"  problem {i} (K {q['K'][0]}, n {q['n']}, nrhs {q['nrhs']}): rel L2 vs oracle {err:.3e}")
         assert err <= 1e-12
+
+
+def test_3d_n4_manufactured_order():
+    """u = sin(pi x) sin(pi y) sin(pi z), f = 3 pi^2 u on the unit cube, n = 4, K = 16..128:
+    f^h on the device (hofem_load), a refined solve (6 fixed corrections), the max dof error
+    against u.  Each
+    halving of h divides it by about 2^{n+1} = 32 (Table 1's n = 4 column: 5.0e-7, 1.6e-8,
+    5.1e-10)."""
+    n = 4
+    errs = []
+    for K in (16, 32, 64, 128):
+        plan = H().Plan(3, [K] * 3, n, [1.0] * 3, H().HOFEM_FP32_REFINED)
+        plan.set_refinement(6)     # solve error ~1e-14, below the K = 128 discretization error
+        xq = torch.tensor(plan.quadrature_points(0), dtype=torch.float64, device="cuda")
+        s = torch.sin(torch.pi * xq)
+        fq = (3.0 * torch.pi ** 2) * s[:, None, None] * s[None, :, None] * s[None, None, :]
+        M = n * K - 1
+        fh = torch.empty((1, M, M, M), dtype=torch.float64, device="cuda")
+        plan.load(fq[None].contiguous(), fh, 1)
+        del fq
+        u = torch.empty_like(fh)
+        plan.solve(fh, u, 1)
+        g = torch.sin(torch.pi * torch.arange(1, M + 1, dtype=torch.float64, device="cuda") / (n * K))
+        err = (u[0] - g[:, None, None] * g[None, :, None] * g[None, None, :]).abs().max().item()
+        errs.append(err)
+        del fh, u
+        plan.close()
+        torch.cuda.empty_cache()
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    print(f"3D n=4 max dof errors {errs}, ratios {ratios}")
+    assert all(0.7 * 32 <= q <= 1.3 * 32 for q in ratios), (errs, ratios)
