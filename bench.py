@@ -217,16 +217,24 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def batch_paths(hofem, torch, stream, tune, steps=3):
+def batch_paths(hofem, torch, stream, tune, steps=3, rank=0, world=1):
     """The batched form: 512 independent 2D problems (K 32..512 and n 2..8 log-uniform, X per
     axis in [0.5, 4], 1-8 RHS each) solved by one CUDA-graph launch per step, FP32 + FP64
-    refinement against the FP64 batch; unknown-RHS per second (the plan is outside the time)."""
+    refinement against the FP64 batch; unknown-RHS per second (the plan is outside the time).
+    Under torchrun the problems are split over the ranks by hofem_batch_partition (predicted
+    work balanced, no collective on the data path); the job's time is the slowest rank's."""
     from paper_1609_07758_gb300 import inputs
-    probs = inputs.batch_problems(4)
+    probs_all = inputs.batch_problems(4)
+    part_of, cost = hofem.batch_partition(probs_all, hofem.HOFEM_FP32_REFINED, world)
+    mine = [i for i in range(len(probs_all)) if part_of[i] == rank]
+    probs = [probs_all[i] for i in mine]
     gen = torch.Generator(device="cuda").manual_seed(4)
-    fs = [torch.randn((q["nrhs"],) + tuple(q["n"] * k - 1 for k in q["K"]), dtype=torch.float64, device="cuda",
-                      generator=gen) for q in probs]
-    out = {"problems": len(probs)}
+    fs_all = [torch.randn((q["nrhs"],) + tuple(q["n"] * k - 1 for k in q["K"]), dtype=torch.float64,
+                          device="cuda", generator=gen) if part_of[i] == rank else None
+              for i, q in enumerate(probs_all)]
+    fs = [fs_all[i] for i in mine]
+    out = {"problems": len(probs_all), "problems_this_rank": len(probs),
+           "predicted_work_per_rank": [sum(c for c, p in zip(cost, part_of) if p == r) for r in range(world)]}
 
     def run(dtype):
         b = hofem.Batch(probs, dtype)
@@ -235,19 +243,24 @@ def batch_paths(hofem, torch, stream, tune, steps=3):
         us = [torch.empty_like(x) for x in fs]
         b.solve(fs, us, stream)                        # capture + first launch
         torch.cuda.synchronize()
+        barrier(world)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
             b.solve(fs, us, stream)
         e1.record(stream)
         torch.cuda.synchronize()
+        barrier(world)
         info = b.info()
         b.close()
-        return e0.elapsed_time(e1) / steps, us, info
+        return max_over_ranks(e0.elapsed_time(e1) / steps, world), us, info
 
     ms_r, ur, info = run(hofem.HOFEM_FP32_REFINED)
     ms_d, ud, _ = run(hofem.HOFEM_FP64)
-    worst = max(float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c)) for a, c in zip(ur, ud))
+    worst = max_over_ranks(max(float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c))
+                               for a, c in zip(ur, ud)), world)
+    total = sum(q["nrhs"] * int(np.prod([q["n"] * k - 1 for k in q["K"]])) for q in probs_all)
+    info.unknowns = total
     out.update({"unknown_rhs": info.unknowns, "graph_nodes": info.graph_nodes,
                 "launch_shapes": "autotuned per problem" if tune else "built-in",
                 "tune_s_refined": info.tune_ms / 1e3,
@@ -502,8 +515,8 @@ def main():
     extras = None
     if args.extras:
         extras = extra_paths(hofem, torch, f, u, stream, args)
-    batched = None if args.no_batch else batch_paths(hofem, torch, stream, args.batch_tune)
-    configs = None if args.no_configs else config_paths(hofem, torch, stream)
+    batched = None if args.no_batch else batch_paths(hofem, torch, stream, args.batch_tune, rank=rank, world=world)
+    configs = None if (args.no_configs or world > 1) else config_paths(hofem, torch, stream)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

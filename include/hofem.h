@@ -318,6 +318,17 @@ hofem_status hofem_batch_solve(hofem_batch_t batch, const double* const* f, doub
 
 hofem_status hofem_batch_get_info(hofem_batch_t batch, hofem_batch_info* out);
 
+/* Split a batch over `parts` GPUs (one process each, no data exchange: the problems are
+ * independent).  part_of[i] receives the part of problem i; cost[i] (if non-NULL) its
+ * predicted work: nrhs x prod_i M_i x ((corrections + 1) (2N - 1)/N sum_i (log2 L_i + n)
+ * + corrections x 2 n N), L_i the FFT length of axis i, corrections the fixed capture count
+ * of `dtype` (0 for unrefined dtypes).  Longest processing time first: problems in
+ * decreasing cost, each to the part with the least predicted work so far, so the parts'
+ * totals differ by at most one problem's cost.  Host only and deterministic (ties by index),
+ * so every rank computes the same split.  part_of, cost: HOST arrays of count entries. */
+hofem_status hofem_batch_partition(int count, const hofem_problem* probs, int dtype, int parts, int* part_of,
+                                   double* cost);
+
 /* The plan of problem i (owned by the batch; for hofem_get_info / hofem_apply). */
 hofem_status hofem_batch_get_plan(hofem_batch_t batch, int i, hofem_plan_t* out);
 void hofem_batch_destroy(hofem_batch_t batch);

@@ -17,6 +17,7 @@ from .binding import (  # noqa: F401
     Batch,
     HofemError,
     Plan,
+    batch_partition,
     hofem_apply,
     hofem_apply_static,
     hofem_autotune,

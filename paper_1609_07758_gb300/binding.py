@@ -23,7 +23,8 @@ EXPORTED = (
     "hofem_residual", "hofem_transform1d", "hofem_get_eigen", "hofem_get_info",
     "hofem_destroy", "hofem_status_string", "hofem_last_error", "hofem_profile", "hofem_get_profile",
     "hofem_apply_static", "hofem_autotune", "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve",
-    "hofem_batch_get_info", "hofem_batch_get_plan", "hofem_batch_destroy", "hofem_quadrature_points",
+    "hofem_batch_get_info", "hofem_batch_get_plan", "hofem_batch_destroy", "hofem_batch_partition",
+    "hofem_quadrature_points",
     "hofem_load", "hofem_lift_dirichlet", "hofem_mass", "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders",
     "hofem_apply_varcoef", "hofem_pcg",
 )
@@ -113,13 +114,16 @@ def load_library():
     lib.hofem_batch_solve.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), V]
     lib.hofem_batch_get_info.argtypes = [P, ctypes.POINTER(hofem_batch_info)]
     lib.hofem_batch_get_plan.argtypes = [P, I, ctypes.POINTER(P)]
+    lib.hofem_batch_partition.argtypes = [I, ctypes.POINTER(hofem_problem), I, I, ctypes.POINTER(I),
+                                          ctypes.POINTER(D)]
     lib.hofem_batch_destroy.argtypes = [P]
     lib.hofem_batch_destroy.restype = None
     for name in ("hofem_plan", "hofem_set_refinement", "hofem_reserve", "hofem_solve", "hofem_apply",
                  "hofem_residual", "hofem_transform1d", "hofem_get_eigen", "hofem_get_info",
                  "hofem_profile", "hofem_get_profile", "hofem_apply_static", "hofem_autotune",
                  "hofem_batch_plan", "hofem_batch_tune", "hofem_batch_solve", "hofem_batch_get_info",
-                 "hofem_batch_get_plan", "hofem_quadrature_points", "hofem_load", "hofem_lift_dirichlet", "hofem_mass",
+                 "hofem_batch_get_plan", "hofem_batch_partition", "hofem_quadrature_points", "hofem_load",
+                 "hofem_lift_dirichlet", "hofem_mass",
                  "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders", "hofem_apply_varcoef",
                  "hofem_pcg"):
         getattr(lib, name).restype = I
@@ -353,20 +357,35 @@ class Plan:
             pass
 
 
+def _problem_array(problems):
+    arr = (hofem_problem * len(problems))()
+    for i, q in enumerate(problems):
+        arr[i].N = int(q["N"])
+        for a in range(int(q["N"])):
+            arr[i].K[a] = int(q["K"][a])
+            arr[i].X[a] = float(q["X"][a])
+        arr[i].n = int(q["n"])
+        arr[i].alpha = float(q.get("alpha", 0.0))
+        arr[i].nrhs = int(q.get("nrhs", 1))
+    return arr
+
+
+def batch_partition(problems, dtype, parts):
+    """(part_of, cost): hofem_batch_partition of a list of problem dicts over `parts` GPUs."""
+    n = len(problems)
+    part_of = (ctypes.c_int * n)()
+    cost = (ctypes.c_double * n)()
+    _check(load_library().hofem_batch_partition(n, _problem_array(problems), int(dtype), int(parts), part_of, cost),
+           "hofem_batch_partition")
+    return list(part_of), list(cost)
+
+
 class Batch:
     """Owns a hofem batch: problems = list of dicts with keys N, K, n, X, alpha, nrhs."""
 
     def __init__(self, problems, dtype=HOFEM_FP32_REFINED):
         lib = load_library()
-        arr = (hofem_problem * len(problems))()
-        for i, q in enumerate(problems):
-            arr[i].N = int(q["N"])
-            for a in range(int(q["N"])):
-                arr[i].K[a] = int(q["K"][a])
-                arr[i].X[a] = float(q["X"][a])
-            arr[i].n = int(q["n"])
-            arr[i].alpha = float(q.get("alpha", 0.0))
-            arr[i].nrhs = int(q.get("nrhs", 1))
+        arr = _problem_array(problems)
         out = ctypes.c_void_p()
         _check(lib.hofem_batch_plan(len(problems), arr, int(dtype), ctypes.byref(out)), "hofem_batch_plan")
         self.handle = out

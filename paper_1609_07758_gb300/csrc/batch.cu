@@ -5,10 +5,12 @@
 // device-wide barrier for.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <string>
 #include <vector>
 
 #include "common.cuh"
+#include "sweep.cuh"
 
 namespace hofem {
 void set_last_error(const std::string& msg);
@@ -103,9 +105,60 @@ hofem_status capture(hofem_batch_s* b, const double* const* f, double* const* u)
   return HOFEM_OK;
 }
 
+// Predicted work of one problem, in units of one unknown-RHS through one axis sweep: each
+// solve sweeps every axis 2N - 1 times at a cost per value of ~log2 of its FFT length plus
+// the order (the per-frequency mixing), and each correction adds the FP64 operator (about
+// two folded element products of order n per axis); refined dtypes run the fixed capture
+// count of corrections (2 when every K is a power of two, else 3; 8 for BF16 / FP16).
+double problem_cost(const hofem_problem& q, int dtype) {
+  double unknowns = q.nrhs, per_value = 0.0, residual = 0.0;
+  bool pow2 = true;
+  for (int i = 0; i < q.N; ++i) {
+    const int K = q.K[i], M = q.n * K - 1;
+    unknowns *= M;
+    pow2 = pow2 && (K & (K - 1)) == 0;
+    const int nb = hofem::bluestein_len(K);
+    const double L = nb > 0 ? nb : K;
+    per_value += std::log2(std::max(L, 2.0)) + q.n;
+    residual += 2.0 * q.n;
+  }
+  const double sweeps = (2.0 * q.N - 1.0) / q.N * per_value;
+  int corr = 0;
+  if (dtype == HOFEM_FP32_REFINED) corr = pow2 ? 2 : 3;
+  if (dtype == HOFEM_BF16_REFINED || dtype == HOFEM_FP16_REFINED) corr = 8;
+  return unknowns * ((corr + 1) * sweeps + corr * residual);
+}
+
 }  // namespace
 
 extern "C" {
+
+hofem_status hofem_batch_partition(int count, const hofem_problem* probs, int dtype, int parts, int* part_of,
+                                   double* cost) {
+  if (count < 1 || !probs || !part_of || parts < 1)
+    return bfail(HOFEM_ERR_INVALID_ARG, "count, parts must be >= 1 and probs, part_of non-NULL");
+  std::vector<double> c(count);
+  for (int i = 0; i < count; ++i) {
+    if ((probs[i].N != 2 && probs[i].N != 3) || probs[i].nrhs < 1 || probs[i].n < 1)
+      return bfail(HOFEM_ERR_INVALID_ARG, "problem " + std::to_string(i) + ": N must be 2 or 3, n and nrhs >= 1");
+    for (int a = 0; a < probs[i].N; ++a)
+      if (probs[i].K[a] < 2) return bfail(HOFEM_ERR_INVALID_ARG, "problem " + std::to_string(i) + ": K must be >= 2");
+    c[i] = problem_cost(probs[i], dtype);
+    if (cost) cost[i] = c[i];
+  }
+  // longest processing time first: problems by decreasing cost (ties by index), each to
+  // the part with the least predicted work so far (ties to the lowest part)
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return c[a] > c[b]; });
+  std::vector<double> load(parts, 0.0);
+  for (int i : order) {
+    const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    part_of[i] = j;
+    load[j] += c[i];
+  }
+  return HOFEM_OK;
+}
 
 hofem_status hofem_batch_plan(int count, const hofem_problem* probs, int dtype, hofem_batch_t* out) {
   const auto t0 = std::chrono::steady_clock::now();

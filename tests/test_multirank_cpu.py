@@ -46,3 +46,42 @@ def test_two_gloo_ranks_share_the_slowest_time_and_solve_different_problems(tmp_
     assert a[3] == b[3] == 15.0                                # max over ranks
     assert a[4] == b[4] == pytest.approx(2 * 100 / 0.015)      # whole-job throughput
     assert a[5] != b[5]                                        # one problem per rank
+
+
+def _partition_rank(rank, world, port, out_dir):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import paper_1609_07758_gb300 as hofem
+    from paper_1609_07758_gb300 import inputs
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    probs = inputs.batch_problems(4)
+    part_of, cost = hofem.batch_partition(probs, hofem.HOFEM_FP32_REFINED, world)
+    mine = [i for i, p in enumerate(part_of) if p == rank]
+    counts = torch.zeros(len(probs), dtype=torch.int64)
+    counts[mine] = 1
+    dist.all_reduce(counts)                         # how many ranks took each problem
+    load = torch.tensor([sum(cost[i] for i in mine)], dtype=torch.float64)
+    loads = [torch.zeros(1, dtype=torch.float64) for _ in range(world)]
+    dist.all_gather(loads, load)
+    np.save(os.path.join(out_dir, f"part{rank}.npy"),
+            np.concatenate([counts.numpy().astype(float), [l.item() for l in loads], [max(cost)]]))
+    dist.destroy_process_group()
+
+
+def test_batch_partition_over_two_gloo_ranks_assigns_each_problem_once_and_balances_cost(tmp_path):
+    """hofem_batch_partition of the 512-problem batch: both ranks compute the same split
+    (host-only, deterministic), every problem lands on exactly one rank, and the ranks'
+    predicted work differs by at most one problem's (longest processing time first)."""
+    import torch.multiprocessing as mp
+    from paper_1609_07758_gb300 import binding
+    if not os.path.exists(binding.library_path()):
+        pytest.skip("libhofem.so is not built")
+    port = _free_port()
+    mp.start_processes(_partition_rank, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn", join=True)
+    a, b = np.load(tmp_path / "part0.npy"), np.load(tmp_path / "part1.npy")
+    assert np.array_equal(a, b)
+    counts, loads, cmax = a[:512], a[512:514], a[514]
+    assert np.all(counts == 1)
+    assert abs(loads[0] - loads[1]) <= cmax
+    assert max(loads) / min(loads) < 1.02
