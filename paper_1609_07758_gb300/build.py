@@ -28,7 +28,7 @@ def nvcc():
 # Sources compiled more than once, each time with one macro: the sweep kernels' FP32 and
 # FP64 instantiations (the longest compile) build in parallel with the host helpers.
 PARTS = {"sweep.cu": ["HOFEM_SWEEP_PART=0", "HOFEM_SWEEP_PART=1", "HOFEM_SWEEP_PART=2"],
-         "sweep_reg.cu": [f"HOFEM_REG_PART={k}" for k in range(5)] + ["HOFEM_REG_PART=100"]}
+         "sweep_reg.cu": [f"HOFEM_REG_PART={k}" for k in range(15)] + ["HOFEM_REG_PART=100"]}
 
 
 def sources():

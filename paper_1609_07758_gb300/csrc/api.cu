@@ -376,9 +376,10 @@ TuneKey apply_key(const hofem_plan_s* p, int axis, int mode, long long nrhs) {
 // The register-resident FP32 sweep serves this sweep: an instantiation exists for the
 // axis' (n, K), the formats are FP32/FP64 without FP16 scaling, and HOFEM_SWEEP_REG is not
 // "0" (which forces the general kernel, for comparisons).
-bool use_reg_sweep(const DevAxis& A, bool f64, int in_fmt, int out_fmt, const unsigned long long* in_amax,
-                   const unsigned long long* out_amax, int* W, int* threads, size_t* smem) {
-  if (f64 || in_amax || out_amax) return false;
+bool use_reg_sweep(const DevAxis& A, bool f64, int mode, bool strided, int in_fmt, int out_fmt,
+                   const unsigned long long* in_amax, const unsigned long long* out_amax, int* W, int* threads,
+                   size_t* smem) {
+  if (f64 || in_amax || out_amax || (mode == kFwdScaleInv && !strided)) return false;
   if ((in_fmt != kFmtF64 && in_fmt != kFmtF32) || (out_fmt != kFmtF64 && out_fmt != kFmtF32)) return false;
   const char* env = getenv("HOFEM_SWEEP_REG");
   if (env && env[0] == '0') return false;
@@ -399,7 +400,7 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
   int W = 1, J = 1, nwarps = 0;
   int rthreads = 0;
   size_t rsmem = 0;
-  const bool reg = use_reg_sweep(A, f64, in_fmt, out_fmt, in_amax, out_amax, &W, &rthreads, &rsmem);
+  const bool reg = use_reg_sweep(A, f64, mode, strided, in_fmt, out_fmt, in_amax, out_amax, &W, &rthreads, &rsmem);
   // the warp-register FFT path is opt-in (HOFEM_WFFT=1): on GB300 it measured slower than
   // the block-wide DIF path (2.5 vs 2.0 ms per sweep at n = 9, K = 1024)
   const char* wf_env = getenv("HOFEM_WFFT");
@@ -841,7 +842,8 @@ hofem_status tune_plan(hofem_plan_s* p, int nrhs, cudaStream_t s, int* measured)
       int rw = 0, rt = 0;
       size_t rs = 0;
       const unsigned long long* am = (!f64 && p->wfmt == kFmtF16) ? p->amax : nullptr;
-      if (use_reg_sweep(A, f64, w.in_fmt, w.out_fmt, am, am, &rw, &rt, &rs)) continue;   // fixed shape
+      if (use_reg_sweep(A, f64, w.mode, std::get<5>(key) == 1, w.in_fmt, w.out_fmt, am, am, &rw, &rt, &rs))
+        continue;   // fixed shape
     }
     const long long lines = std::get<7>(key);
     const bool strided = std::get<5>(key) == 1;

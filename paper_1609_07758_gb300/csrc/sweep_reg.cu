@@ -29,8 +29,36 @@
 #ifndef HOFEM_REG_PART
 #define HOFEM_REG_PART -1
 #endif
+#if HOFEM_REG_PART == 100
+#pragma nv_diag_suppress 177   // the table part uses only some members of the shape structs
+#endif
 
 namespace hofem {
+namespace {
+// Compile-time shape of one instantiation.
+template <int N_, int LOGK_, int W_, int NW_> struct RegCfg {
+  static constexpr int N = N_, LOGK = LOGK_, W = W_, NW = NW_;
+  static constexpr int K = 1 << LOGK, L = K / 32, T = 32 / L, G = 32 / L;
+  static constexpr int M = N * K - 1;
+  static constexpr int PAIRS = (N - 1) / 2;
+  static constexpr int NJOBS = W * PAIRS + ((N % 2 == 0) ? W : (W + 1) / 2);
+  static constexpr int NT = 32 * NW;
+  // line stride in the tile: >= M and = 32 / W (mod 32) for W | 32, so that the strided
+  // loads (W consecutive lines per row) write distinct banks
+  static constexpr int MSR = (W >= 1 && W <= 32 && (32 % W) == 0) ? (32 / W) % 32 : 1;
+  static constexpr int MS = M + ((MSR - M % 32) % 32 + 32) % 32;
+  static constexpr int WIN = 32 * 33 * 2;          // floats of one warp's transpose area
+  static constexpr int TF = (W * MS + 3) & ~3;
+  static constexpr int SCR = NW * WIN;
+  static constexpr int ROUNDS = (NJOBS + NW * G - 1) / (NW * G);   // job rounds per CTA
+  static constexpr int SAVE = ((W * (N > 1 ? N - 1 : 1)) + 3) & ~3;
+  static constexpr int LR = (W + 3) & ~3;
+  static constexpr size_t SMEM = (size_t)(TF + SCR + SAVE + LR) * 4 + (size_t)NW * 8;
+  static_assert(LOGK >= 6 && LOGK <= 10, "K = 64 .. 1024");
+};
+
+}  // namespace
+
 #if HOFEM_REG_PART != 100
 namespace {
 
@@ -123,28 +151,6 @@ template <int R> __device__ __forceinline__ void dft(float2 (&v)[R]) {
     }
   }
 }
-
-// Compile-time shape of one instantiation.
-template <int N_, int LOGK_, int W_, int NW_> struct RegCfg {
-  static constexpr int N = N_, LOGK = LOGK_, W = W_, NW = NW_;
-  static constexpr int K = 1 << LOGK, L = K / 32, T = 32 / L, G = 32 / L;
-  static constexpr int M = N * K - 1;
-  static constexpr int PAIRS = (N - 1) / 2;
-  static constexpr int NJOBS = W * PAIRS + ((N % 2 == 0) ? W : (W + 1) / 2);
-  static constexpr int NT = 32 * NW;
-  // line stride in the tile: >= M and = 32 / W (mod 32) for W | 32, so that the strided
-  // loads (W consecutive lines per row) write distinct banks
-  static constexpr int MSR = (W >= 1 && W <= 32 && (32 % W) == 0) ? (32 / W) % 32 : 1;
-  static constexpr int MS = M + ((MSR - M % 32) % 32 + 32) % 32;
-  static constexpr int WIN = 32 * 33 * 2;          // floats of one warp's transpose area
-  static constexpr int TF = (W * MS + 3) & ~3;
-  static constexpr int SCR = NW * WIN;
-  static constexpr int ROUNDS = (NJOBS + NW * G - 1) / (NW * G);   // job rounds per CTA
-  static constexpr int SAVE = ((W * (N > 1 ? N - 1 : 1)) + 3) & ~3;
-  static constexpr int LR = (W + 3) & ~3;
-  static constexpr size_t SMEM = (size_t)(TF + SCR + SAVE + LR) * 4 + (size_t)NW * 8;
-  static_assert(LOGK >= 6 && LOGK <= 10, "K = 64 .. 1024");
-};
 
 struct RJob {
   int wa, ca, wb, cb;   // component c of line w; c = 0: nodes; cb < 0: absent
@@ -413,10 +419,13 @@ __device__ __forceinline__ void mixing(float* tile, float* save, const float* lr
   __syncthreads();
 }
 
-template <int N, int LOGK, int W, int NW, int MINB>
+// One sweep of MODE (kFwd, kFwdScaleInv or kInv) over contiguous (CONTIG) or strided lines.
+template <int N, int LOGK, int W, int NW, int MINB, int MODE, bool CONTIG>
 __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepParams P) {
   using C = RegCfg<N, LOGK, W, NW>;
   constexpr int M = C::M, MS = C::MS, NT = C::NT, K = C::K;
+  static_assert((W & (W - 1)) == 0, "W is a power of two");
+  constexpr int LW = W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : W == 16 ? 4 : 5;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* tile = reinterpret_cast<float*>(smem_raw);
   float* scr = tile + C::TF;
@@ -427,58 +436,70 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
   double* red = reinterpret_cast<double*>(lrest + C::LR);
   const int tid = threadIdx.x;
 
-  const bool contiguous = (P.inner == 1);
   const long long b = blockIdx.x;
   const long long o = b / P.tiles_per_outer, tix = b - o * P.tiles_per_outer;
   const long long l0 = tix * W;
-  const long long nl = contiguous ? P.outer_per_rhs : P.inner;
+  const long long nl = CONTIG ? P.outer_per_rhs : P.inner;
   const int wvalid = (int)(nl - l0 < W ? nl - l0 : W);
-  const long long rhs = contiguous ? o : o / P.outer_per_rhs;
-  const long long gbase = contiguous ? (o * P.outer_per_rhs + l0) * (long long)M : o * (long long)M * P.inner + l0;
+  const long long rhs = CONTIG ? o : o / P.outer_per_rhs;
+  const long long gbase = CONTIG ? (o * P.outer_per_rhs + l0) * (long long)M : o * (long long)M * P.inner + l0;
   const long long inner = P.inner;
 
-  // ---- load W lines (missing lines read as zeros).  Element e is (line w, position p):
-  // e = w M + p (contiguous lines) or e = p W + w (strided columns).  The loads of an
-  // unrolled group are unconditional (out-of-range elements read the tile's first element)
-  // so that they are all in flight at once.
+  // ---- load W lines (missing lines read as zeros).  Contiguous lines go line by line
+  // (position p = p0 + u NT, no index division); strided tiles as elements e = p W + w.
+  // The loads of an unrolled group are unconditional at clamped valid addresses, so that
+  // they are all in flight at once.
   constexpr int TOT = W * M, U = 16, UL = 32;
-  auto decode = [&](int e, int& w, int& p) {
-    if (contiguous) { w = e / M; p = e - w * M; }
-    else { w = e % W; p = e / W; }
-  };
-  auto gaddr = [&](int w, int p) -> long long { return contiguous ? gbase + (long long)w * M + p : gbase + p * inner + w; };
   if (P.in_fmt == kFmtF64) {
-    // FP64 input (narrowed on the way): UL loads per thread in flight in registers
     const double* __restrict__ in = (const double*)P.in;
-    for (int e0 = tid; e0 < TOT; e0 += UL * NT) {
-      double v[UL];
+    if constexpr (CONTIG) {
+      for (int w = 0; w < W; ++w) {
+        const bool lv = w < wvalid;
+        const double* src = in + gbase + (long long)(lv ? w : 0) * M;
+        for (int p0 = tid; p0 < M; p0 += UL * NT) {
+          double v[UL];
 #pragma unroll
-      for (int u = 0; u < UL; ++u) {
-        int w, p;
-        decode(e0 + u * NT, w, p);
-        const bool ok = e0 + u * NT < TOT && w < wvalid;
-        v[u] = __ldg(in + (ok ? gaddr(w, p) : gbase));
+          for (int u = 0; u < UL; ++u) v[u] = __ldg(src + (p0 + u * NT < M ? p0 + u * NT : 0));
+#pragma unroll
+          for (int u = 0; u < UL; ++u)
+            if (p0 + u * NT < M) tile[w * MS + p0 + u * NT] = lv ? (float)v[u] : 0.f;
+        }
       }
+    } else {
+      for (int e0 = tid; e0 < TOT; e0 += UL * NT) {
+        double v[UL];
 #pragma unroll
-      for (int u = 0; u < UL; ++u) {
-        int w, p;
-        decode(e0 + u * NT, w, p);
-        if (e0 + u * NT < TOT) tile[w * MS + p] = w < wvalid ? (float)v[u] : 0.f;
+        for (int u = 0; u < UL; ++u) {
+          const int e = e0 + u * NT, w = e & (W - 1), p = e >> LW;
+          v[u] = __ldg(in + ((e < TOT && w < wvalid) ? gbase + p * inner + w : gbase));
+        }
+#pragma unroll
+        for (int u = 0; u < UL; ++u) {
+          const int e = e0 + u * NT, w = e & (W - 1), p = e >> LW;
+          if (e < TOT) tile[w * MS + p] = w < wvalid ? (float)v[u] : 0.f;
+        }
       }
     }
   } else {
     // FP32 input: asynchronous 4-byte copies straight into the tile (zero-filled for the
     // missing lines), the whole tile in flight at once
     const float* __restrict__ in = (const float*)P.in;
-    for (int e = tid; e < TOT; e += NT) {
-      int w, p;
-      decode(e, w, p);
-      const bool ok = w < wvalid;
-      cp_async4(tile + w * MS + p, in + (ok ? gaddr(w, p) : gbase), ok ? 4 : 0);
+    if constexpr (CONTIG) {
+      for (int w = 0; w < W; ++w) {
+        const bool lv = w < wvalid;
+        const float* src = in + gbase + (long long)(lv ? w : 0) * M;
+        for (int p = tid; p < M; p += NT) cp_async4(tile + w * MS + p, src + p, lv ? 4 : 0);
+      }
+    } else {
+      for (int e = tid; e < TOT; e += NT) {
+        const int w = e & (W - 1), p = e >> LW;
+        const bool ok = w < wvalid;
+        cp_async4(tile + w * MS + p, in + (ok ? gbase + p * inner + w : gbase), ok ? 4 : 0);
+      }
     }
     cp_async_wait_all();
   }
-  if (P.mode == kFwdScaleInv) {
+  if constexpr (MODE == kFwdScaleInv) {
     for (int w = tid; w < W; w += NT) {
       const long long c = l0 + w;
       float rest = 0.f;
@@ -492,7 +513,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
   }
   __syncthreads();
 
-  if (P.mode & kFwd) {
+  if constexpr ((MODE & kFwd) != 0) {
     // k = 0 sums t_i = sum_j (-P)^{j-1} y_{j-1/2}, component i, one warp per (line, i)
     if constexpr (N > 1) {
       const int lane = tid & 31, wid = tid >> 5;
@@ -509,23 +530,19 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
       }
     }
     dst_jobs<C, true>(tile, scr, twx, twz);
-    if (P.mode == kFwd) mixing<C, kFwd>(tile, save, lrest, P);
-    else mixing<C, kFwdScaleInv>(tile, save, lrest, P);
-  } else {
-    mixing<C, kInv>(tile, save, lrest, P);
   }
-  if (P.mode & kInv) dst_jobs<C, false>(tile, scr, twx, twz);
+  mixing<C, MODE>(tile, save, lrest, P);
+  if constexpr ((MODE & kInv) != 0) dst_jobs<C, false>(tile, scr, twx, twz);
 
   // ---- store: spectral tile (direct sweep) or the post-combine of the inverse transform,
   //   v_j = D_j (nodes),  v_{j-1/2,c} = D_{j-1,c} + D_{j,N-c} + (-1)^{j-1} g_{c or N-c}
-  const bool inv = (P.mode & kInv) != 0;
+  constexpr bool inv = (MODE & kInv) != 0;
   const bool want_norm = P.norms != nullptr;
   float s_d = 0.f;
   auto value = [&](int w, int p) -> float {
     const float* t = tile + w * MS;
-    if (!inv) return t[p];
+    if (!inv || N == 1) return t[p];
     const int j = p / N + 1, c = p - (j - 1) * N + 1;
-    if (N == 1) return t[p];
     // clamped reads, masked: D_{j-1, c} (j >= 2), D_{j, N-c} (j <= K-1), g (c < N)
     const int cc = c < N ? c : 1;
     const float d0 = t[j >= 2 ? p - N : p], d1 = t[j <= K - 1 ? p + N - 2 * cc : p];
@@ -536,36 +553,65 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
   };
   if (P.out_fmt == kFmtF64) {
     double* out = (double*)P.out;
-    for (int e0 = tid; e0 < TOT; e0 += U * NT) {
-      double prev[U];
-      if (P.accumulate) {
+    if constexpr (CONTIG) {
+      for (int w = 0; w < wvalid; ++w) {
+        double* dst = out + gbase + (long long)w * M;
+        for (int p0 = tid; p0 < M; p0 += U * NT) {
+          double prev[U];
+          if (P.accumulate) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          int w, p;
-          decode(e0 + u * NT, w, p);
-          const bool ok = e0 + u * NT < TOT && w < wvalid;
-          prev[u] = out[ok ? gaddr(w, p) : gbase];
+            for (int u = 0; u < U; ++u) prev[u] = dst[p0 + u * NT < M ? p0 + u * NT : 0];
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int p = p0 + u * NT;
+            if (p < M) {
+              const float tv = value(w, p);
+              dst[p] = P.accumulate ? prev[u] + (double)tv : (double)tv;
+              if (want_norm) s_d = fmaf(tv, tv, s_d);
+            }
+          }
         }
       }
+    } else {
+      for (int e0 = tid; e0 < TOT; e0 += U * NT) {
+        double prev[U];
+        if (P.accumulate) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int w, p;
-        decode(e0 + u * NT, w, p);
-        if (e0 + u * NT < TOT && w < wvalid) {
-          const float tv = value(w, p);
-          out[gaddr(w, p)] = P.accumulate ? prev[u] + (double)tv : (double)tv;
-          if (want_norm) s_d = fmaf(tv, tv, s_d);
+          for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * NT, w = e & (W - 1), p = e >> LW;
+            prev[u] = out[(e < TOT && w < wvalid) ? gbase + p * inner + w : gbase];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + u * NT, w = e & (W - 1), p = e >> LW;
+          if (e < TOT && w < wvalid) {
+            const float tv = value(w, p);
+            out[gbase + p * inner + w] = P.accumulate ? prev[u] + (double)tv : (double)tv;
+            if (want_norm) s_d = fmaf(tv, tv, s_d);
+          }
         }
       }
     }
   } else {
     float* out = (float*)P.out;
-    for (int e0 = tid; e0 < TOT; e0 += U * NT) {
+    if constexpr (CONTIG) {
+      for (int w = 0; w < wvalid; ++w) {
+        float* dst = out + gbase + (long long)w * M;
+        for (int p0 = tid; p0 < M; p0 += U * NT) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int w, p;
-        decode(e0 + u * NT, w, p);
-        if (e0 + u * NT < TOT && w < wvalid) out[gaddr(w, p)] = value(w, p);
+          for (int u = 0; u < U; ++u)
+            if (p0 + u * NT < M) dst[p0 + u * NT] = value(w, p0 + u * NT);
+        }
+      }
+    } else {
+      for (int e0 = tid; e0 < TOT; e0 += U * NT) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + u * NT, w = e & (W - 1), p = e >> LW;
+          if (e < TOT && w < wvalid) out[gbase + p * inner + w] = value(w, p);
+        }
       }
     }
   }
@@ -587,49 +633,84 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
 }  // namespace
 #endif
 
-// ---- instantiations: (id, order, log2 K, lines per CTA, warps per CTA, CTAs per SM).
-// The build compiles this file once per instantiation (HOFEM_REG_PART = id) and once for
-// the dispatch table (HOFEM_REG_PART = 100), so the kernels compile in parallel; without the
-// macro one object holds everything.
-#define HOFEM_REG_LIST(X)                                                               \
-  X(0, 9, 10, 4, 9, 1)   /* 2D n = 9, K = 1024 (9215^2 unknowns): 18 jobs, 2 rounds of 9 */ \
-  X(1, 9, 10, 1, 5, 2)   /* same shape, one line per CTA, two CTAs per SM */            \
-  X(2, 9, 10, 2, 9, 1)   /* same shape, two lines per CTA */                            \
-  X(3, 4, 7, 16, 4, 3)   /* 3D n = 4, K = 128 */                                        \
-  X(4, 8, 6, 16, 4, 3)   /* 3D n = 8, K = 64 */
+// ---- instantiations: (id, order, log2 K, lines per CTA, warps per CTA, CTAs per SM), each
+// with five kernels: forward on contiguous / strided lines, the fused sweep (always on the
+// strided axis 0), inverse on contiguous / strided lines.  The build compiles this file once
+// per kernel (HOFEM_REG_PART = 5 id + kernel) and once for the dispatch table
+// (HOFEM_REG_PART = 100), so the kernels compile in parallel; without the macro one object
+// holds everything.
+#define HOFEM_REG_LIST(X) \
+  X(0, 9, 10, 4, 9, 1)   /* 2D n = 9, K = 1024 (9215^2 unknowns): 18 jobs, 2 rounds of 9 warps */ \
+  X(1, 4, 7, 16, 4, 3)   /* 3D n = 4, K = 128 */ \
+  X(2, 8, 6, 16, 4, 3)   /* 3D n = 8, K = 64 */
 
-#define HOFEM_REG_DECL(ID, NN, LK, WW, NWW, MB)                      \
-  cudaError_t reg_launch_##ID(const SweepParams& p, cudaStream_t s); \
-  cudaError_t reg_attr_##ID();                                      \
-  size_t reg_smem_##ID();
+#define HOFEM_REG_DECL(ID, NN, LK, WW, NWW, MB)                                                \
+  cudaError_t reg_attr_##ID##_0(); cudaError_t reg_attr_##ID##_1(); cudaError_t reg_attr_##ID##_2(); \
+  cudaError_t reg_attr_##ID##_3(); cudaError_t reg_attr_##ID##_4();                            \
+  cudaError_t reg_launch_##ID##_0(const SweepParams& p, cudaStream_t s);                       \
+  cudaError_t reg_launch_##ID##_1(const SweepParams& p, cudaStream_t s);                       \
+  cudaError_t reg_launch_##ID##_2(const SweepParams& p, cudaStream_t s);                       \
+  cudaError_t reg_launch_##ID##_3(const SweepParams& p, cudaStream_t s);                       \
+  cudaError_t reg_launch_##ID##_4(const SweepParams& p, cudaStream_t s);
 HOFEM_REG_LIST(HOFEM_REG_DECL)
 #undef HOFEM_REG_DECL
 
-#define HOFEM_REG_DEF(ID, NN, LK, WW, NWW, MB)                                                           \
-  cudaError_t reg_launch_##ID(const SweepParams& p, cudaStream_t s) {                                   \
-    sweep_reg_kernel<NN, LK, WW, NWW, MB><<<(unsigned)p.ntiles, 32 * NWW, RegCfg<NN, LK, WW, NWW>::SMEM, s>>>(p); \
+#define HOFEM_REG_DEF(ID, KI, NN, LK, WW, NWW, MB, MODE, CONTIG)                                          \
+  cudaError_t reg_launch_##ID##_##KI(const SweepParams& p, cudaStream_t s) {                           \
+    sweep_reg_kernel<NN, LK, WW, NWW, MB, MODE, CONTIG>                                                \
+        <<<(unsigned)p.ntiles, 32 * NWW, RegCfg<NN, LK, WW, NWW>::SMEM, s>>>(p);                       \
     return cudaGetLastError();                                                                          \
   }                                                                                                     \
-  cudaError_t reg_attr_##ID() {                                                                         \
-    return cudaFuncSetAttribute(sweep_reg_kernel<NN, LK, WW, NWW, MB>,                                  \
+  cudaError_t reg_attr_##ID##_##KI() {                                                                  \
+    return cudaFuncSetAttribute(sweep_reg_kernel<NN, LK, WW, NWW, MB, MODE, CONTIG>,                   \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
                                 (int)RegCfg<NN, LK, WW, NWW>::SMEM);                                    \
-  }                                                                                                     \
-  size_t reg_smem_##ID() { return RegCfg<NN, LK, WW, NWW>::SMEM; }
+  }
+
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 0
-HOFEM_REG_DEF(0, 9, 10, 4, 9, 1)
+HOFEM_REG_DEF(0, 0, 9, 10, 4, 9, 1, kFwd, true)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 1
-HOFEM_REG_DEF(1, 9, 10, 1, 5, 2)
+HOFEM_REG_DEF(0, 1, 9, 10, 4, 9, 1, kFwd, false)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 2
-HOFEM_REG_DEF(2, 9, 10, 2, 9, 1)
+HOFEM_REG_DEF(0, 2, 9, 10, 4, 9, 1, kFwdScaleInv, false)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 3
-HOFEM_REG_DEF(3, 4, 7, 16, 4, 3)
+HOFEM_REG_DEF(0, 3, 9, 10, 4, 9, 1, kInv, true)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 4
-HOFEM_REG_DEF(4, 8, 6, 16, 4, 3)
+HOFEM_REG_DEF(0, 4, 9, 10, 4, 9, 1, kInv, false)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 5
+HOFEM_REG_DEF(1, 0, 4, 7, 16, 4, 3, kFwd, true)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 6
+HOFEM_REG_DEF(1, 1, 4, 7, 16, 4, 3, kFwd, false)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 7
+HOFEM_REG_DEF(1, 2, 4, 7, 16, 4, 3, kFwdScaleInv, false)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 8
+HOFEM_REG_DEF(1, 3, 4, 7, 16, 4, 3, kInv, true)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 9
+HOFEM_REG_DEF(1, 4, 4, 7, 16, 4, 3, kInv, false)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 10
+HOFEM_REG_DEF(2, 0, 8, 6, 16, 4, 3, kFwd, true)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 11
+HOFEM_REG_DEF(2, 1, 8, 6, 16, 4, 3, kFwd, false)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 12
+HOFEM_REG_DEF(2, 2, 8, 6, 16, 4, 3, kFwdScaleInv, false)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 13
+HOFEM_REG_DEF(2, 3, 8, 6, 16, 4, 3, kInv, true)
+#endif
+#if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 14
+HOFEM_REG_DEF(2, 4, 8, 6, 16, 4, 3, kInv, false)
 #endif
 
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 100
@@ -637,26 +718,31 @@ namespace {
 
 struct RegEntry {
   int n, logK, W, nw;
-  cudaError_t (*launch)(const SweepParams&, cudaStream_t);
-  cudaError_t (*attr)();
-  size_t (*smem)();
+  size_t smem;
+  cudaError_t (*launch[5])(const SweepParams&, cudaStream_t);
+  cudaError_t (*attr[5])();
 };
 
-#define HOFEM_REG_ENTRY(ID, NN, LK, WW, NWW, MB) RegEntry{NN, LK, WW, NWW, reg_launch_##ID, reg_attr_##ID, reg_smem_##ID},
+#define HOFEM_REG_ENTRY(ID, NN, LK, WW, NWW, MB)                                                  \
+  RegEntry{NN, LK, WW, NWW, RegCfg<NN, LK, WW, NWW>::SMEM,                                      \
+           {reg_launch_##ID##_0, reg_launch_##ID##_1, reg_launch_##ID##_2, reg_launch_##ID##_3, \
+            reg_launch_##ID##_4},                                                               \
+           {reg_attr_##ID##_0, reg_attr_##ID##_1, reg_attr_##ID##_2, reg_attr_##ID##_3, reg_attr_##ID##_4}},
 const RegEntry kRegTable[] = {HOFEM_REG_LIST(HOFEM_REG_ENTRY)};
 #undef HOFEM_REG_ENTRY
 
-// The first instantiation listed for (n, K), or the one with HOFEM_SWEEP_REG_W lines per CTA.
 const RegEntry* reg_entry(int n, int K) {
-  int wantW = 0;
-  if (const char* e = getenv("HOFEM_SWEEP_REG_W")) wantW = atoi(e);
-  const RegEntry* first = nullptr;
-  for (const RegEntry& e : kRegTable) {
-    if (e.n != n || (1 << e.logK) != K) continue;
-    if (!first) first = &e;
-    if (wantW > 0 && e.W == wantW) return &e;
-  }
-  return first;
+  for (const RegEntry& e : kRegTable)
+    if (e.n == n && (1 << e.logK) == K) return &e;
+  return nullptr;
+}
+
+// kernel index of a sweep: forward contiguous / strided, fused (strided), inverse
+// contiguous / strided; -1: no kernel (a fused sweep on contiguous lines)
+int reg_kernel_index(int mode, bool contiguous) {
+  if (mode == kFwd) return contiguous ? 0 : 1;
+  if (mode == kFwdScaleInv) return contiguous ? -1 : 2;
+  return contiguous ? 3 : 4;
 }
 
 }  // namespace
@@ -666,22 +752,24 @@ bool sweep_reg_shape(int n, int K, int* W, int* threads, size_t* smem) {
   if (!e) return false;
   *W = e->W;
   *threads = 32 * e->nw;
-  *smem = e->smem();
+  *smem = e->smem;
   return true;
 }
 
 cudaError_t sweep_reg_set_smem_limits() {
-  for (const RegEntry& e : kRegTable) {
-    cudaError_t r = e.attr();
-    if (r != cudaSuccess) return r;
-  }
+  for (const RegEntry& e : kRegTable)
+    for (int k = 0; k < 5; ++k) {
+      cudaError_t r = e.attr[k]();
+      if (r != cudaSuccess) return r;
+    }
   return cudaSuccess;
 }
 
 cudaError_t launch_sweep_reg(const SweepParams& p, cudaStream_t s) {
   const RegEntry* e = reg_entry(p.n, p.K);
-  if (!e || e->W != p.W) return cudaErrorInvalidValue;
-  return e->launch(p, s);
+  const int k = reg_kernel_index(p.mode, p.inner == 1);
+  if (!e || e->W != p.W || k < 0) return cudaErrorInvalidValue;
+  return e->launch[k](p, s);
 }
 #endif
 

@@ -5,8 +5,7 @@ The transform hook runs W lines per CTA over a number of lines that leaves the l
 ragged; the solves run it on contiguous and strided axes, several right-hand sides,
 mixed orders per axis, next to axes on the general kernel, unrefined (FP32, 1e-5) and
 refined (1e-12).  HOFEM_SWEEP_REG=0 forces the general kernel on the same plan, which both
-paths are also compared against; HOFEM_SWEEP_REG_W picks the instantiation with that many
-lines per CTA where there are two.
+paths are also compared against.
 """
 import numpy as np
 import pytest
@@ -53,10 +52,8 @@ def transforms(plan, y, c, lines, M):
     return fwd, out.cpu().numpy()
 
 
-@pytest.mark.parametrize("n,K,lines,W", [(9, 1024, 5, 4), (9, 1024, 5, 2), (9, 1024, 3, 1), (4, 128, 37, 16),
-                                         (8, 64, 21, 16)])
+@pytest.mark.parametrize("n,K,lines,W", [(9, 1024, 5, 4), (9, 1024, 3, 4), (4, 128, 37, 16), (8, 64, 21, 16)])
 def test_register_sweep_transforms_match_oracle(monkeypatch, n, K, lines, W):
-    monkeypatch.setenv("HOFEM_SWEEP_REG_W", str(W))
     X = 1.3
     plan = H().Plan(2, [K, K], n, [X, X], H().HOFEM_FP32)
     s = spectrum.spectrum(n, K, X)
