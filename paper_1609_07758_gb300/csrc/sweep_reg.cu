@@ -359,7 +359,7 @@ __device__ __forceinline__ void mixing(float* tile, float* save, const float* lr
         if (MODE == kFwdScaleInv) {
           const float rw = lrest[w];
 #pragma unroll
-          for (int l = 0; l < N; ++l) x[l] = y[l] * __frcp_rn(lq[l] + rw);
+          for (int l = 0; l < N; ++l) x[l] = __fdividef(y[l], lq[l] + rw);   // ~2 ulp, refined
         }
       }
       if (MODE & kInv) {
