@@ -52,8 +52,9 @@ def parse_args():
                     help="skip the 3D workloads (n=4 K=128; n=8 K=64 with 16 RHS), refined vs FP64")
     ap.add_argument("--batch-tune", action="store_true",
                     help="autotune every problem of the batch first (84 s for 512 problems; 3%% faster solves)")
-    ap.add_argument("--extras", action="store_true",
-                    help="also time on-device f^h, algorithm (b) and a heat step at the same size")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the widened paths at the same size (on-device f^h, algorithm (b), a heat "
+                         "step, the variable-coefficient operator and PCG)")
     ap.add_argument("--elements", type=int, default=K_ELEM,
                     help="elements per axis (default 1024, the benchmark workload; smaller K for profiling)")
     args = ap.parse_args()
@@ -340,6 +341,13 @@ def extra_paths(hofem, torch, f, u, stream, args):
     fq = torch.ones((1, G, G), dtype=torch.float64, device="cuda")
     out["load_fh_ms"] = time_ms(lambda: p64.load(fq, u, 1, stream))
     out["solve_banded_fp64_ms"] = time_ms(lambda: p64.solve_banded(f, u, 1, stream))
+    # the banded solves alone (two per call: the solve and its FP64-residual correction)
+    p64.profile(1)
+    p64.solve_banded(f, u, 1, stream)
+    prof = p64.get_profile()
+    p64.profile(0)
+    if "banded_f64" in prof:
+        out["banded_kernels_ms_per_solve"] = prof["banded_f64"][1] / prof["banded_f64"][0]
     ph = hofem.Plan(2, K2, N_ORDER, X2, hofem.HOFEM_FP32_REFINED, alpha=100.0)
     uh = f.clone()
     out["heat_step_refined_ms"] = time_ms(lambda: ph.heat_steps(uh, 1, 1, stream=stream))
@@ -513,7 +521,7 @@ def main():
     else:
         ms_e2e, ms_e2e_serial = e2e_time(plan, f_host, f, stream, args, world, torch)
     extras = None
-    if args.extras:
+    if not args.no_extras and world == 1:
         extras = extra_paths(hofem, torch, f, u, stream, args)
     batched = None if args.no_batch else batch_paths(hofem, torch, stream, args.batch_tune, rank=rank, world=world)
     configs = None if (args.no_configs or world > 1) else config_paths(hofem, torch, stream)

@@ -122,7 +122,8 @@ typedef struct {
 typedef struct {
   char name[32];            /* "sweep_{fwd,fsi,inv}_{f64,f32}" (general sweep kernel, FP64 or FP32
                                work), "sweep_{fwd,fsi,inv}_reg" (register-resident FP32 sweep),
-                               "apply_f64" (operator sweep) */
+                               "apply_f64" (operator sweep), "banded_f64" (the banded solves
+                               of algorithm (b)) */
   int launches;
   double total_ms;
 } hofem_kernel_time;

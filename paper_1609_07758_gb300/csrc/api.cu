@@ -110,11 +110,11 @@ struct hofem_plan_s {
 namespace {
 
 // kinds 0-5: the general sweep kernel (FP64 / FP32 work), 6: the FP64 operator sweep,
-// 7-9: the register-resident FP32 sweep
+// 7-9: the register-resident FP32 sweep, 10: the banded solves of algorithm (b)
 const char* const kKindNames[] = {"sweep_fwd_f64", "sweep_fsi_f64", "sweep_inv_f64", "sweep_fwd_f32",
                                   "sweep_fsi_f32", "sweep_inv_f32", "apply_f64",     "sweep_fwd_reg",
-                                  "sweep_fsi_reg", "sweep_inv_reg"};
-constexpr int kNumKinds = 10;
+                                  "sweep_fsi_reg", "sweep_inv_reg", "banded_f64"};
+constexpr int kNumKinds = 11;
 
 cudaEvent_t pool_event(hofem_plan_s* p) {
   if (!p->pool.empty()) {
@@ -666,8 +666,11 @@ hofem_status banded_once(hofem_plan_s* p, const double* f, double* u, int nrhs, 
     B.A[i] = A0.h.Aloc[i];
     B.C[i] = A0.h.Cloc[i];
   }
-  HOFEM_CUDA(launch_banded(B, s), "banded solve launch");
-  p->info.kernel_launches += 1;
+  {
+    cudaError_t e = timed_launch(p, 10, s, [&]() { return launch_banded(B, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "banded solve launch");
+    p->info.kernel_launches += B.n > 1 ? 2 : 0;   // three kernels for n >= 2 (one counted above)
+  }
   // FP64 inverse transforms back along x_2..x_N
   for (int a = 1; a <= N - 1; ++a)
     if ((st = run_sweep(p, a, kInv, true, u, kFmtF64, u, kFmtF64, false, nullptr, nrhs, s)) != HOFEM_OK) return st;

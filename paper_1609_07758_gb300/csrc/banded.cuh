@@ -8,7 +8,8 @@ constexpr int kBandTab = (kMaxN + 1) * (kMaxN + 1);
 
 struct BandParams {
   double* u;                  // (outer, M, inner): transformed RHS in, solution out (in place)
-  double* scratch;            // outer x inner x K doubles: Thomas multipliers per node
+  double* scratch;            // outer x inner x (K + 2 ceil(K / 32)) doubles: Thomas multipliers
+                              // per node and the chunk-boundary node contributions
   long long outer, inner;
   int K, n, M;
   double sA;                  // 4 h^-2 of the solve axis

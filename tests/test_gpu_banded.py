@@ -1,5 +1,7 @@
 """Algorithm (b) (hofem_solve_banded): transforms along x_2..x_N and banded solves per mode
-along x_1 reach the same discrete solution as the oracle's tensor-product solve."""
+along x_1 reach the same discrete solution as the oracle's tensor-product solve.  For n >= 2
+the banded solve condenses chunks of 32 elements in parallel; K_1 = 65, 100 and 257 give
+several chunks and a ragged last one."""
 import numpy as np
 import pytest
 
@@ -32,6 +34,10 @@ CASES = [
     (2, 9, [16, 16], [1.0, 1.0], 0.0, 2),
     (3, 2, [8, 8, 8], [1.0, 1.0, 1.0], 0.0, 2),
     (3, 3, [6, 5, 9], [1.0, 0.6, 2.0], 0.5, 1),
+    # several 32-element condensation chunks along x_1, the last one ragged
+    (2, 9, [100, 8], [1.0, 1.0], 0.0, 1),
+    (2, 2, [257, 3], [1.2, 1.0], 0.3, 2),
+    (3, 4, [65, 3, 2], [1.0, 1.0, 0.5], 0.0, 1),
 ]
 
 
