@@ -545,13 +545,18 @@ hofem_status solve_once(hofem_plan_s* p, const double* f, double* u, int nrhs, b
 // One operator sweep along `axis` (modes in residual.cuh): Q == nullptr is the first
 // sweep (out1 required), Q and out1 a middle one, Q without out1 the last one.
 hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double* Q_, double* out1, double* out2,
-                       const double* f, double cA, double cCP, int nrhs, cudaStream_t s) {
+                       const double* f, double cA, double cCP, int nrhs, cudaStream_t s, bool uniform = false) {
   const DevAxis& A = p->ax[axis];
   Geo g = geometry(p, axis);
   const bool strided = g.inner > 1;
   ApplyParams P{};
   const int W = kApplyLines;
-  int E = 16;   // elements per CTA: measured best of 4 / 8 / 16 at n = 9, K = 1024
+  // elements per CTA: the largest of 16 / 8 / 4 whose tile lets three CTAs share an SM
+  // (orders compiled for it), else 16 halved below to fit (measured best at n = 9, K = 1024:
+  // E = 8 at three CTAs per SM)
+  int E = 16;
+  if (A.h.n <= kApplyMinb3MaxN)
+    while (E > 4 && apply_smem_bytes(A.h.n, E) > kApplySmem3) E /= 2;
   {
     int tE = 0, unused = 0;
     const TuneKey key = apply_key(p, axis, Q_ == nullptr ? kApplyFirst : (out1 ? kApplyMid : kApplyLast), nrhs);
@@ -586,6 +591,7 @@ hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double
   P.f = f;
   P.cA = cA * A.h.a_scale;
   P.cCP = cCP;
+  P.uniform = uniform ? 1 : 0;
   std::copy(A.h.CfE.begin(), A.h.CfE.end(), P.CE);
   std::copy(A.h.CfO.begin(), A.h.CfO.end(), P.CO);
   std::copy(A.h.AfE.begin(), A.h.AfE.end(), P.AE);
@@ -599,6 +605,17 @@ hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double
   return HOFEM_OK;
 }
 
+// True when every axis has the same stiffness coefficient 4 h_i^-2 / D_i (exact integer
+// tables, n_i <= 9): the operator sweeps then carry unscaled sums and the last one scales.
+bool uniform_stiffness(const hofem_plan_s* p, const double* sc) {
+  const double c0 = sc[0] * p->ax[0].h.a_scale;
+  for (int i = 0; i < p->N; ++i) {
+    const AxisTables& h = p->ax[i].h;
+    if (h.n > kExactStiffnessMaxN || h.a_scale == 1.0 || sc[i] * h.a_scale != c0) return false;
+  }
+  return c0 != 0.0;
+}
+
 // out = A u (f == nullptr) or out = f - A u, Eq. bvp glob 2, by one sweep per axis.
 hofem_status operator_apply(hofem_plan_s* p, const double* u, const double* f, double* out, int nrhs,
                             cudaStream_t s) {
@@ -608,6 +625,17 @@ hofem_status operator_apply(hofem_plan_s* p, const double* u, const double* f, d
   double sc[3];
   for (int i = 0; i < N; ++i) sc[i] = 4.0 * (double)p->K[i] * (double)p->K[i] / (p->X[i] * p->X[i]);
   double** t = p->tmp64;
+  if (uniform_stiffness(p, sc)) {
+    // A u = c (sum_i A_i x prod_{m != i} C_m + alpha / c prod C_m), c applied by the last sweep
+    const double c = sc[0] * p->ax[0].h.a_scale, ac = p->alpha / c;
+    if (N == 2) {
+      if ((st = run_apply(p, 1, u, nullptr, t[0], t[1], nullptr, sc[1], ac, nrhs, s, true)) != HOFEM_OK) return st;
+      return run_apply(p, 0, t[0], t[1], nullptr, out, f, sc[0], 0.0, nrhs, s, true);
+    }
+    if ((st = run_apply(p, 2, u, nullptr, t[0], t[1], nullptr, sc[2], ac, nrhs, s, true)) != HOFEM_OK) return st;
+    if ((st = run_apply(p, 1, t[0], t[1], t[2], t[3], nullptr, sc[1], 0.0, nrhs, s, true)) != HOFEM_OK) return st;
+    return run_apply(p, 0, t[2], t[3], nullptr, out, f, sc[0], 0.0, nrhs, s, true);
+  }
   if (N == 2) {
     // axis 1: T1 = u xC, T2 = s1 (u xA) + alpha (u xC); axis 0: out = [f -] (s0 T1 xA + T2 xC)
     if ((st = run_apply(p, 1, u, nullptr, t[0], t[1], nullptr, sc[1], p->alpha, nrhs, s)) != HOFEM_OK) return st;

@@ -20,6 +20,14 @@
 // Folding: with w_e[t] = w_t + w_{n-t}, w_o[t] = w_t - w_{n-t} (t < h = (n+1)/2) and the
 // middle value for even n, rows r and n-r of M w are E_r + O_r and E_r - O_r, which
 // halves the products.  The odd part of the differences is w_o itself.
+//
+// Uniform scale (US): when every axis has the same stiffness coefficient c (same h_i and
+// exact integer tables of the same order), the operator is c (sum_i A_i x prod C_m) +
+// alpha prod C_m, and the sweeps carry the sums unscaled: the first sweep writes P x A
+// (+ alpha / c P x C), a middle one P x A + Q x C, and the last one accumulates P x A and
+// Q x C in one register per row and writes f - c v (or c v).  That removes one FP64
+// multiply per output row of the first sweep and one combining operation per row of the
+// later ones.
 #include "common.cuh"
 #include "residual.cuh"
 
@@ -34,7 +42,7 @@ constexpr int kLd = kApplyLines + 1;   // tile row stride in doubles (odd: no ba
 // (outer-product order), so only the row accumulators and one folded pair are live.
 // Interior rows are written back into the tiles in place (tP <- P x C, tQ <- out2),
 // which only this element reads; rows 0 and n go to the slot arrays for the node sums.
-template <int N, int MODE, bool HALO>
+template <int N, int MODE, bool HALO, bool US>
 __device__ __forceinline__ void element_rows(const ApplyParams& P, double* tP, double* tQ, int base, int w,
                                              double* sV0, double* sP0, double* sVn, double* sPn, int s) {
   constexpr int n = N, h = (N + 1) / 2, hr = N / 2 + 1;
@@ -42,6 +50,8 @@ __device__ __forceinline__ void element_rows(const ApplyParams& P, double* tP, d
   constexpr bool LO = N > kExactStiffnessMaxN;
   constexpr bool PC = MODE != kApplyLast;    // P x C is wanted
   constexpr bool QC = MODE != kApplyFirst;   // Q x C is wanted
+  constexpr bool QS = QC && !US;             // Q x C in accumulators of its own
+  static_assert(!(US && LO), "uniform-scale sweeps use exact integer stiffness tables");
   constexpr int rE = HALO ? 1 : hr, rO = HALO ? 1 : h;   // rows computed
   double cE[hr], cO[h], aE[hr], aO[h], qE[hr], qO[h];
   float lE[hr], lO[h];
@@ -57,13 +67,14 @@ __device__ __forceinline__ void element_rows(const ApplyParams& P, double* tP, d
         if (PC) cE[r] = ce * pe;
         aE[r] = ae * de;
         if (LO) lE[r] = P.AEl[r * hr + t] * (float)de;
-        if (QC) qE[r] = ce * qe;
+        if (QS) qE[r] = ce * qe;
       } else {
         if (PC) cE[r] = fma(ce, pe, cE[r]);
         aE[r] = fma(ae, de, aE[r]);
         if (LO) lE[r] = fmaf(P.AEl[r * hr + t], (float)de, lE[r]);
-        if (QC) qE[r] = fma(ce, qe, qE[r]);
+        if (QS) qE[r] = fma(ce, qe, qE[r]);
       }
+      if (US && QC) aE[r] = fma(ce, qe, aE[r]);
     }
     if (middle) return;
 #pragma unroll
@@ -73,13 +84,14 @@ __device__ __forceinline__ void element_rows(const ApplyParams& P, double* tP, d
         if (PC) cO[r] = co * po;
         aO[r] = ao * po;
         if (LO) lO[r] = P.AOl[r * h + t] * (float)po;
-        if (QC) qO[r] = co * qo;
+        if (QS) qO[r] = co * qo;
       } else {
         if (PC) cO[r] = fma(co, po, cO[r]);
         aO[r] = fma(ao, po, aO[r]);
         if (LO) lO[r] = fmaf(P.AOl[r * h + t], (float)po, lO[r]);
-        if (QC) qO[r] = fma(co, qo, qO[r]);
+        if (QS) qO[r] = fma(co, qo, qO[r]);
       }
+      if (US && QC) aO[r] = fma(co, qo, aO[r]);
     }
   };
 #pragma unroll
@@ -118,9 +130,15 @@ __device__ __forceinline__ void element_rows(const ApplyParams& P, double* tP, d
       if (r < h) ao += (double)lO[r];
     }
     const double ce = PC ? cE[r] : 0.0, co = PC && r < h ? cO[r] : 0.0;
-    // even and odd parts of out2
-    double se = QC ? fma(cA, ae, qE[r]) : cA * ae;
-    double so = r < h ? (QC ? fma(cA, ao, qO[r]) : cA * ao) : 0.0;
+    // even and odd parts of out2 (unscaled sums under a uniform scale)
+    double se, so;
+    if (US) {
+      se = ae;
+      so = r < h ? ao : 0.0;
+    } else {
+      se = QC ? fma(cA, ae, qE[r]) : cA * ae;
+      so = r < h ? (QC ? fma(cA, ao, qO[r]) : cA * ao) : 0.0;
+    }
     if (alpha) {
       se = fma(cCP, ce, se);
       if (r < h) so = fma(cCP, co, so);
@@ -138,8 +156,12 @@ __device__ __forceinline__ void element_rows(const ApplyParams& P, double* tP, d
 // left node of the segment .. right node of the halo element j0+E (row 0 of which closes
 // the segment's last node).  Loads and stores are coalesced along whichever of line or
 // dof index is contiguous in memory.
-template <int N, int MODE>
-__global__ void __launch_bounds__(kApplyThreads, N <= 10 ? 2 : 1) apply_kernel(const __grid_constant__ ApplyParams P) {
+// Orders up to kApplyMinb3MaxN are compiled for three CTAs per SM (at most 85 registers a
+// thread, E chosen so that the tile fits a third of shared memory): the FP64 pipe then has
+// 24 warps to draw from while some CTAs load or store (measured 7.6% faster than two CTAs
+// at n = 9, K = 1024).
+template <int N, int MODE, bool US>
+__global__ void __launch_bounds__(kApplyThreads, N <= kApplyMinb3MaxN ? 3 : N <= 10 ? 2 : 1) apply_kernel(const __grid_constant__ ApplyParams P) {
   constexpr int n = N, W = kApplyLines;
   constexpr bool PC = MODE != kApplyLast, QC = MODE != kApplyFirst;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -185,10 +207,10 @@ __global__ void __launch_bounds__(kApplyThreads, N <= 10 ? 2 : 1) apply_kernel(c
   __syncthreads();
   for (int it = threadIdx.x; it < E * W; it += blockDim.x) {
     const int e = it / W, w = it - e * W;
-    element_rows<N, MODE, false>(P, tP, tQ, e * n, w, sV0, sP0, sVn, sPn, it);
+    element_rows<N, MODE, false, US>(P, tP, tQ, e * n, w, sV0, sP0, sVn, sPn, it);
   }
   for (int w = threadIdx.x; w < W; w += blockDim.x)
-    element_rows<N, MODE, true>(P, tP, tQ, E * n, w, sV0, sP0, sVn, sPn, E * W + w);
+    element_rows<N, MODE, true, US>(P, tP, tQ, E * n, w, sV0, sP0, sVn, sPn, E * W + w);
   __syncthreads();
   // node rows (e+1) n: row n of element e + row 0 of element e+1
   for (int it = threadIdx.x; it < E * W; it += blockDim.x) {
@@ -198,24 +220,45 @@ __global__ void __launch_bounds__(kApplyThreads, N <= 10 ? 2 : 1) apply_kernel(c
     if (PC) tP[row] = sPn[it] + sP0[it + W];
   }
   __syncthreads();
-  // tile rows 1 .. E n are this segment's dofs
-  const int Rs = E * n;
-  for (int it = threadIdx.x; it < Rs * W; it += blockDim.x) {
-    int r, w;
-    if (contiguous) {
-      w = it / Rs;
-      r = it - w * Rs + 1;
-    } else {
-      r = it / W + 1;
-      w = it - (r - 1) * W;
+  // tile rows 1 .. E n are this segment's dofs; f of a group of U entries is read before
+  // any of them is stored (clamped valid addresses, masked), so those loads overlap
+  const int Rs = E * n, total = Rs * W;
+  constexpr int U = 4;
+  const bool use_f = MODE == kApplyLast && P.f != nullptr;
+  for (int it0 = threadIdx.x; it0 < total; it0 += U * blockDim.x) {
+    int rr[U], ww[U];
+    bool ok[U];
+    size_t gg[U];
+    double fv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int it = it0 + u * blockDim.x;
+      int r, w;
+      if (contiguous) {
+        w = it / Rs;
+        r = it - w * Rs + 1;
+      } else {
+        r = it / W + 1;
+        w = it - (r - 1) * W;
+      }
+      const long long p = p0 + r;
+      ok[u] = it < total && w < wvalid && p < M;
+      rr[u] = r;
+      ww[u] = w;
+      gg[u] = ok[u] ? gidx(p, w) : 0;
+      fv[u] = use_f ? __ldg(P.f + gg[u]) : 0.0;
     }
-    const long long p = p0 + r;
-    if (w >= wvalid || p >= M) continue;
-    const size_t g = gidx(p, w);
-    double v = tQ[(size_t)r * kLd + w];
-    if (MODE == kApplyLast && P.f) v = __ldg(P.f + g) - v;
-    P.out2[g] = v;
-    if (PC) P.out1[g] = tP[(size_t)r * kLd + w];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!ok[u]) continue;
+      double v = tQ[(size_t)rr[u] * kLd + ww[u]];
+      if (MODE == kApplyLast) {
+        if (US) v = use_f ? fma(-P.cA, v, fv[u]) : P.cA * v;
+        else if (use_f) v = fv[u] - v;
+      }
+      P.out2[gg[u]] = v;
+      if (PC) P.out1[gg[u]] = tP[(size_t)rr[u] * kLd + ww[u]];
+    }
   }
 }
 
@@ -226,12 +269,19 @@ size_t apply_smem_bytes(int n, int E) {
   return (2 * R * kLd + 2 * (size_t)(E + 1) * kApplyLines + 2 * (size_t)E * kApplyLines) * sizeof(double);
 }
 
+template <int N, bool US> static cudaError_t set_limit_us() {
+  cudaError_t e = cudaFuncSetAttribute(apply_kernel<N, kApplyFirst, US>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(apply_kernel<N, kApplyMid, US>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(apply_kernel<N, kApplyLast, US>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  return e;
+}
+
 template <int N> static cudaError_t set_limit() {
-  cudaError_t e = cudaFuncSetAttribute(apply_kernel<N, kApplyFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(apply_kernel<N, kApplyMid>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(apply_kernel<N, kApplyLast>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  cudaError_t e = set_limit_us<N, false>();
+  if constexpr (N <= kExactStiffnessMaxN)
+    if (e == cudaSuccess) e = set_limit_us<N, true>();
   return e;
 }
 
@@ -245,17 +295,28 @@ cudaError_t apply_set_smem_limits() {
   return e;
 }
 
-template <int N> static void launch_n(const ApplyParams& p, cudaStream_t s) {
+template <int N, bool US> static void launch_us(const ApplyParams& p, cudaStream_t s) {
   const dim3 grid((unsigned)p.ntiles), block(kApplyThreads);
   switch (p.mode) {
-    case kApplyFirst: apply_kernel<N, kApplyFirst><<<grid, block, p.smem_bytes, s>>>(p); break;
-    case kApplyMid: apply_kernel<N, kApplyMid><<<grid, block, p.smem_bytes, s>>>(p); break;
-    default: apply_kernel<N, kApplyLast><<<grid, block, p.smem_bytes, s>>>(p); break;
+    case kApplyFirst: apply_kernel<N, kApplyFirst, US><<<grid, block, p.smem_bytes, s>>>(p); break;
+    case kApplyMid: apply_kernel<N, kApplyMid, US><<<grid, block, p.smem_bytes, s>>>(p); break;
+    default: apply_kernel<N, kApplyLast, US><<<grid, block, p.smem_bytes, s>>>(p); break;
   }
+}
+
+template <int N> static void launch_n(const ApplyParams& p, cudaStream_t s) {
+  if constexpr (N <= kExactStiffnessMaxN) {
+    if (p.uniform) {
+      launch_us<N, true>(p, s);
+      return;
+    }
+  }
+  launch_us<N, false>(p, s);
 }
 
 cudaError_t launch_apply(const ApplyParams& p, cudaStream_t s) {
   if (p.mode < kApplyFirst || p.mode > kApplyLast) return cudaErrorInvalidValue;
+  if (p.uniform && p.n > kExactStiffnessMaxN) return cudaErrorInvalidValue;
   switch (p.n) {
 #define HOFEM_AP_CASE(NN) \
   case NN: launch_n<NN>(p, s); break;

@@ -13,16 +13,24 @@ constexpr int kFoldO = ((kMaxN + 1) / 2) * ((kMaxN + 1) / 2);
 //   kApplyFirst: out1 = P x C,  out2 = cA (P x A) + cCP (P x C)
 //   kApplyMid:   out1 = P x C,  out2 = cA (P x A) + cCP (P x C) + Q x C
 //   kApplyLast:                 out2 = [f -] (cA (P x A) + Q x C)
+// With `uniform` set (every axis has the coefficient cA, exact integer stiffness tables):
+//   kApplyFirst: out1 = P x C,  out2 = P x A + cCP (P x C)       (cCP = alpha / cA)
+//   kApplyMid:   out1 = P x C,  out2 = P x A + Q x C
+//   kApplyLast:                 out2 = [f -] cA (P x A + Q x C)
 enum ApplyMode { kApplyFirst = 0, kApplyMid = 1, kApplyLast = 2 };
 
 constexpr int kApplyThreads = 256;
 constexpr int kApplyLines = 32;            // lines per CTA (W)
+constexpr int kApplyMinb3MaxN = 9;         // orders compiled for three CTAs per SM
+constexpr size_t kApplySmem3 = 232448 / 3 - 1024;   // shared memory per CTA at three per SM
 
 struct ApplyParams {
   long long outer, inner, outer_per_rhs;   // same geometry as the transform sweeps
   long long tiles_per_outer, seg_per_line, ntiles;
   int M, n, K, W, E;                       // W lines per CTA, E elements per segment
   int mode;                                // ApplyMode
+  int uniform;                             // every axis has the same stiffness coefficient:
+                                           // out2 unscaled, cA applied by the last sweep
   const double* P;
   const double* Q;                         // kApplyMid, kApplyLast
   double* out1;                            // kApplyFirst, kApplyMid

@@ -29,6 +29,9 @@
 #ifndef HOFEM_REG_PART
 #define HOFEM_REG_PART -1
 #endif
+#ifndef HOFEM_REG_MIX
+#define HOFEM_REG_MIX 0
+#endif
 #if HOFEM_REG_PART == 100
 #pragma nv_diag_suppress 177   // the table part uses only some members of the shape structs
 #endif
@@ -55,6 +58,10 @@ template <int N_, int LOGK_, int W_, int NW_> struct RegCfg {
   static constexpr int LR = (W + 3) & ~3;
   static constexpr size_t SMEM = (size_t)(TF + SCR + SAVE + LR) * 4 + (size_t)NW * 8;
   static_assert(LOGK >= 6 && LOGK <= 10, "K = 64 .. 1024");
+  // per-frequency mixing form (HOFEM_REG_MIX): 0 one thread per frequency over all lines,
+  // 1 one thread per (frequency, group of up to 4 lines), 2 tensor cores (3xTF32
+  // m16n8k8) where n = 8 and the lines come in groups of 16, else form 1
+  static constexpr int MIX = HOFEM_REG_MIX == 2 ? ((N == 8 && W % 16 == 0) ? 2 : 1) : HOFEM_REG_MIX;
 };
 
 }  // namespace
@@ -326,14 +333,108 @@ __device__ __forceinline__ void dst_jobs(float* tile, float* scr, const float2* 
 // kFwdScaleInv (both, with the division by lam + rest between them).  G_k is read from the
 // frequency-fastest copy of the table (consecutive threads, consecutive addresses) into
 // registers and applied to the lines one by one.
+// FP32 value as a TF32 operand (round to nearest, ties away) and the TF32 remainder
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+  const float r = x - __uint_as_float(hi);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
+// d += a b for one m16n8k8 TF32 tile (FP32 accumulate)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// d = a b with a, b split into TF32 hi + lo: hi hi + hi lo + lo hi (the lo lo term and
+// the remainders are ~2^-22 relative), small terms first
+__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const float (&a)[4], const float (&b)[2]) {
+  uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) split_tf32(a[i], ah[i], al[i]);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) split_tf32(b[i], bh[i], bl[i]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) d[i] = 0.f;
+  mma_tf32(d, al, bh);
+  mma_tf32(d, ah, bl);
+  mma_tf32(d, ah, bh);
+}
+
+// Per-frequency mixing of n = 8 on the tensor cores: for frequency k and 16 lines, the
+// forward Y = X G_k^T / 2K (X: lines x components, A operand from the tile; B[s][l] =
+// G_k[l][s]) and the inverse Y = X G_k / 2 (B[l][s] = G_k[l][s]), one warp per
+// (frequency, 16 lines).  Fragment layouts of m16n8k8: lane = 4 g + t holds A rows g,
+// g + 8 and columns t, t + 4; B row (k) t, t + 4 and column g; C rows g, g + 8 and columns
+// 2t, 2t + 1.  The fused sweep divides the C fragment and passes it to the inverse
+// product through the warp's own tile slots.
+template <class C, int MODE>
+__device__ __forceinline__ void mixing_tc(float* tile, const float* lrest, const SweepParams& P) {
+  constexpr int N = C::N, K = C::K, KM = C::K - 1;
+  static_assert(N == 8 && C::W % 16 == 0, "tensor-core mixing: n = 8, 16 lines per group");
+  const float* __restrict__ mt = P.mixT;
+  const float* __restrict__ lt = P.lamT;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  for (int item = wid; item < KM * (C::W / 16); item += C::NW) {
+    const int kk = item % KM, wb = (item / KM) * 16;
+    float* r0 = tile + (wb + g) * C::MS + kk * N;
+    float* r1 = r0 + 8 * C::MS;
+    float a[4] = {r0[t], r1[t], r0[t + 4], r1[t + 4]};
+    float d[4];
+    if (MODE & kFwd) {
+      const float b[2] = {__ldg(mt + (g * N + t) * KM + kk), __ldg(mt + (g * N + t + 4) * KM + kk)};
+      mma_3xtf32(d, a, b);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) d[i] *= 0.5f / K;
+      if (MODE == kFwdScaleInv) {
+        const float l0 = __ldg(lt + (2 * t) * KM + kk), l1 = __ldg(lt + (2 * t + 1) * KM + kk);
+        const float w0 = lrest[wb + g], w1 = lrest[wb + g + 8];
+        d[0] = __fdividef(d[0], l0 + w0);   // ~2 ulp, refined
+        d[1] = __fdividef(d[1], l1 + w0);
+        d[2] = __fdividef(d[2], l0 + w1);
+        d[3] = __fdividef(d[3], l1 + w1);
+        __syncwarp();
+        r0[2 * t] = d[0];
+        r0[2 * t + 1] = d[1];
+        r1[2 * t] = d[2];
+        r1[2 * t + 1] = d[3];
+        __syncwarp();
+        a[0] = r0[t];
+        a[1] = r1[t];
+        a[2] = r0[t + 4];
+        a[3] = r1[t + 4];
+      }
+    }
+    if (MODE & kInv) {
+      const float b[2] = {__ldg(mt + (t * N + g) * KM + kk), __ldg(mt + ((t + 4) * N + g) * KM + kk)};
+      mma_3xtf32(d, a, b);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) d[i] *= 0.5f;
+    }
+    __syncwarp();
+    r0[2 * t] = d[0];
+    r0[2 * t + 1] = d[1];
+    r1[2 * t] = d[2];
+    r1[2 * t + 1] = d[3];
+  }
+}
+
 template <class C, int MODE>
 __device__ __forceinline__ void mixing(float* tile, float* save, const float* lrest, const SweepParams& P) {
   constexpr int N = C::N, K = C::K, W = C::W, KM = C::K - 1;
   const float* __restrict__ mt = P.mixT;
   const float* __restrict__ lt = P.lamT;
   const float* __restrict__ lam = (const float*)P.lam;
-  for (int k = 1 + (int)threadIdx.x; k < K; k += C::NT) {
-    const int kk = k - 1, base = kk * N;
+  // lines per work item of the scalar forms
+  constexpr int LG = C::MIX == 0 ? W : (W < 4 ? W : 4);
+  constexpr int NIT = C::MIX == 2 ? 0 : KM * (W / LG);
+  if constexpr (C::MIX == 2) mixing_tc<C, MODE>(tile, lrest, P);
+  for (int item = (int)threadIdx.x; item < NIT; item += C::NT) {
+    const int kk = item % KM, wl = (item / KM) * LG, base = kk * N;
     float G[N][N], lq[N];
 #pragma unroll
     for (int l = 0; l < N; ++l)
@@ -343,8 +444,8 @@ __device__ __forceinline__ void mixing(float* tile, float* save, const float* lr
 #pragma unroll
       for (int l = 0; l < N; ++l) lq[l] = __ldg(lt + l * KM + kk);
     }
-#pragma unroll(W <= 4 ? W : 1)
-    for (int w = 0; w < W; ++w) {
+#pragma unroll(LG <= 4 ? LG : 1)
+    for (int w = wl; w < wl + LG; ++w) {
       float x[N], y[N];
 #pragma unroll
       for (int s = 0; s < N; ++s) x[s] = tile[w * C::MS + base + s];
@@ -419,14 +520,14 @@ __device__ __forceinline__ void mixing(float* tile, float* save, const float* lr
   __syncthreads();
 }
 
-// One sweep of MODE (kFwd, kFwdScaleInv or kInv) over contiguous (CONTIG) or strided lines.
+// One tile (W lines) of a sweep of MODE (kFwd, kFwdScaleInv or kInv) over contiguous
+// (CONTIG) or strided lines.
 template <int N, int LOGK, int W, int NW, int MINB, int MODE, bool CONTIG>
-__global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepParams P) {
+__device__ __forceinline__ void reg_tile(const SweepParams& P, const long long b, unsigned char* smem_raw) {
   using C = RegCfg<N, LOGK, W, NW>;
   constexpr int M = C::M, MS = C::MS, NT = C::NT, K = C::K;
   static_assert((W & (W - 1)) == 0, "W is a power of two");
   constexpr int LW = W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : W == 16 ? 4 : 5;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   float* tile = reinterpret_cast<float*>(smem_raw);
   float* scr = tile + C::TF;
   float* save = scr + C::SCR;
@@ -436,7 +537,6 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
   double* red = reinterpret_cast<double*>(lrest + C::LR);
   const int tid = threadIdx.x;
 
-  const long long b = blockIdx.x;
   const long long o = b / P.tiles_per_outer, tix = b - o * P.tiles_per_outer;
   const long long l0 = tix * W;
   const long long nl = CONTIG ? P.outer_per_rhs : P.inner;
@@ -630,6 +730,13 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
   }
 }
 
+// One sweep of MODE over contiguous (CONTIG) or strided lines: one CTA per tile of W lines.
+template <int N, int LOGK, int W, int NW, int MINB, int MODE, bool CONTIG>
+__global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  reg_tile<N, LOGK, W, NW, MINB, MODE, CONTIG>(P, blockIdx.x, smem_raw);
+}
+
 }  // namespace
 #endif
 
@@ -639,10 +746,26 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
 // per kernel (HOFEM_REG_PART = 5 id + kernel) and once for the dispatch table
 // (HOFEM_REG_PART = 100), so the kernels compile in parallel; without the macro one object
 // holds everything.
+// (order, log2 K, lines per CTA, warps per CTA, CTAs per SM) of each id.  A build may
+// time another launch shape of the n = 9, K = 1024 kernels with -DHOFEM_REG0_W=...,
+// -DHOFEM_REG0_NW=..., -DHOFEM_REG0_MB=...
+#ifndef HOFEM_REG0_W
+#define HOFEM_REG0_W 4
+#endif
+#ifndef HOFEM_REG0_NW
+#define HOFEM_REG0_NW 9
+#endif
+#ifndef HOFEM_REG0_MB
+#define HOFEM_REG0_MB 1
+#endif
+#define HOFEM_REG_SHAPE0 9, 10, HOFEM_REG0_W, HOFEM_REG0_NW, HOFEM_REG0_MB   /* 2D n = 9, K = 1024 (9215^2 unknowns) */
+#define HOFEM_REG_SHAPE1 4, 7, 16, 4, 3                                      /* 3D n = 4, K = 128 */
+#define HOFEM_REG_SHAPE2 8, 6, 16, 4, 3                                      /* 3D n = 8, K = 64 */
+#define HOFEM_REG_CALL(X, ...) X(__VA_ARGS__)
 #define HOFEM_REG_LIST(X) \
-  X(0, 9, 10, 4, 9, 1)   /* 2D n = 9, K = 1024 (9215^2 unknowns): 18 jobs, 2 rounds of 9 warps */ \
-  X(1, 4, 7, 16, 4, 3)   /* 3D n = 4, K = 128 */ \
-  X(2, 8, 6, 16, 4, 3)   /* 3D n = 8, K = 64 */
+  HOFEM_REG_CALL(X, 0, HOFEM_REG_SHAPE0) \
+  HOFEM_REG_CALL(X, 1, HOFEM_REG_SHAPE1) \
+  HOFEM_REG_CALL(X, 2, HOFEM_REG_SHAPE2)
 
 #define HOFEM_REG_DECL(ID, NN, LK, WW, NWW, MB)                                                \
   cudaError_t reg_attr_##ID##_0(); cudaError_t reg_attr_##ID##_1(); cudaError_t reg_attr_##ID##_2(); \
@@ -667,50 +790,54 @@ HOFEM_REG_LIST(HOFEM_REG_DECL)
                                 (int)RegCfg<NN, LK, WW, NWW>::SMEM);                                    \
   }
 
+// the id, kernel index, mode and layout first, so that the shape macro can close the list
+#define HOFEM_REG_DEF_S(ID, KI, MODE, CONTIG, NN, LK, WW, NWW, MB) \
+  HOFEM_REG_DEF(ID, KI, NN, LK, WW, NWW, MB, MODE, CONTIG)
+
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 0
-HOFEM_REG_DEF(0, 0, 9, 10, 4, 9, 1, kFwd, true)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 0, 0, kFwd, true, HOFEM_REG_SHAPE0)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 1
-HOFEM_REG_DEF(0, 1, 9, 10, 4, 9, 1, kFwd, false)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 0, 1, kFwd, false, HOFEM_REG_SHAPE0)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 2
-HOFEM_REG_DEF(0, 2, 9, 10, 4, 9, 1, kFwdScaleInv, false)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 0, 2, kFwdScaleInv, false, HOFEM_REG_SHAPE0)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 3
-HOFEM_REG_DEF(0, 3, 9, 10, 4, 9, 1, kInv, true)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 0, 3, kInv, true, HOFEM_REG_SHAPE0)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 4
-HOFEM_REG_DEF(0, 4, 9, 10, 4, 9, 1, kInv, false)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 0, 4, kInv, false, HOFEM_REG_SHAPE0)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 5
-HOFEM_REG_DEF(1, 0, 4, 7, 16, 4, 3, kFwd, true)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 1, 0, kFwd, true, HOFEM_REG_SHAPE1)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 6
-HOFEM_REG_DEF(1, 1, 4, 7, 16, 4, 3, kFwd, false)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 1, 1, kFwd, false, HOFEM_REG_SHAPE1)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 7
-HOFEM_REG_DEF(1, 2, 4, 7, 16, 4, 3, kFwdScaleInv, false)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 1, 2, kFwdScaleInv, false, HOFEM_REG_SHAPE1)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 8
-HOFEM_REG_DEF(1, 3, 4, 7, 16, 4, 3, kInv, true)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 1, 3, kInv, true, HOFEM_REG_SHAPE1)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 9
-HOFEM_REG_DEF(1, 4, 4, 7, 16, 4, 3, kInv, false)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 1, 4, kInv, false, HOFEM_REG_SHAPE1)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 10
-HOFEM_REG_DEF(2, 0, 8, 6, 16, 4, 3, kFwd, true)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 2, 0, kFwd, true, HOFEM_REG_SHAPE2)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 11
-HOFEM_REG_DEF(2, 1, 8, 6, 16, 4, 3, kFwd, false)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 2, 1, kFwd, false, HOFEM_REG_SHAPE2)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 12
-HOFEM_REG_DEF(2, 2, 8, 6, 16, 4, 3, kFwdScaleInv, false)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 2, 2, kFwdScaleInv, false, HOFEM_REG_SHAPE2)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 13
-HOFEM_REG_DEF(2, 3, 8, 6, 16, 4, 3, kInv, true)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 2, 3, kInv, true, HOFEM_REG_SHAPE2)
 #endif
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 14
-HOFEM_REG_DEF(2, 4, 8, 6, 16, 4, 3, kInv, false)
+HOFEM_REG_CALL(HOFEM_REG_DEF_S, 2, 4, kInv, false, HOFEM_REG_SHAPE2)
 #endif
 
 #if HOFEM_REG_PART < 0 || HOFEM_REG_PART == 100
