@@ -282,6 +282,36 @@ hofem_status hofem_residual(hofem_plan_t plan, const double* f, const double* u,
 hofem_status hofem_transform1d(hofem_plan_t plan, int axis, int inverse, const double* in,
                                double* out, long lines, void* stream);
 
+/* Sweep kinds of hofem_sweep. */
+enum { HOFEM_SWEEP_FORWARD = 0, HOFEM_SWEEP_FUSED = 1, HOFEM_SWEEP_INVERSE = 2 };
+
+/* One sweep of algorithm (a) (Sect. 2 par. 4) along `axis` on a block of lines that need
+ * not be the plan's whole grid -- the building block of one problem split over several
+ * GPUs by slabs of x_1 (each GPU transforms the axes it holds whole, an all-to-all
+ * exchange makes x_1 whole, and so on).  in, out: device FP64 arrays laid out as
+ * [outer][M_axis][inner] (C order; in == out allowed): `outer` blocks of `inner` lines.
+ *   HOFEM_SWEEP_FORWARD: the direct F_n-transform of every line (Theorem 2 part 2, as
+ *     hofem_transform1d with inverse = 0);
+ *   HOFEM_SWEEP_INVERSE: the inverse one (Theorem 2 part 1);
+ *   HOFEM_SWEEP_FUSED (axis 0 only): direct transform, division of coefficient q of line
+ *     l by lam_1[q] + sum_{i>=2} lam_i[q_i(c)] + alpha (Eq. decomp v 2), where the line's
+ *     column c = line_offset + l indexes the x_2..x_N plane in C order (c = q_2 for N = 2,
+ *     c = q_2 M_3 + q_3 for N = 3), then the inverse transform.  line_offset + inner must
+ *     not exceed the plane's size; nrhs > 1 is outer = nrhs with the same columns.
+ * Runs in the plan's precision: FP64 plans in FP64, FP32 (unrefined) plans in FP32
+ * arithmetic with FP64 input and output; other dtypes return HOFEM_ERR_UNSUPPORTED.
+ * Asynchronous on stream. */
+hofem_status hofem_sweep(hofem_plan_t plan, int axis, int mode, const double* in, double* out,
+                         long long outer, long long inner, long long line_offset, void* stream);
+
+/* dst[b][r][c] = src[b][r][c] for b < batch, r < rows, c < cols, with element offsets
+ * b src_bs + r src_ld + c (and the dst_* ones): the packing and unpacking of the blocks an
+ * all-to-all exchange moves between GPUs.  Device FP64 pointers, not overlapping.
+ * Asynchronous on stream. */
+hofem_status hofem_copy_block(const double* src, double* dst, long long batch, long long rows, long long cols,
+                              long long src_ld, long long dst_ld, long long src_bs, long long dst_bs,
+                              void* stream);
+
 /* Test hook: copy axis `axis`'s eigen-data to HOST buffers (any may be NULL):
  * lam[M] true eigenvalues 4 h^-2 lambda_q in spectral order; mix[(K-1) n n]: row l of
  * block k-1 is (q_1..q_{n-1}, c) of mode (k, l) (interior values then the nodal

@@ -14,6 +14,9 @@ from .binding import (  # noqa: F401
     HOFEM_FP32,
     HOFEM_FP32_REFINED,
     HOFEM_FP64,
+    HOFEM_SWEEP_FORWARD,
+    HOFEM_SWEEP_FUSED,
+    HOFEM_SWEEP_INVERSE,
     Batch,
     HofemError,
     Plan,
@@ -21,6 +24,7 @@ from .binding import (  # noqa: F401
     hofem_apply,
     hofem_apply_static,
     hofem_autotune,
+    hofem_copy_block,
     hofem_destroy,
     hofem_get_eigen,
     hofem_get_info,
@@ -33,6 +37,7 @@ from .binding import (  # noqa: F401
     hofem_set_refinement,
     hofem_solve,
     hofem_status_string,
+    hofem_sweep,
     hofem_transform1d,
     library_path,
     load_library,

@@ -26,7 +26,7 @@ EXPORTED = (
     "hofem_batch_get_info", "hofem_batch_get_plan", "hofem_batch_destroy", "hofem_batch_partition",
     "hofem_quadrature_points",
     "hofem_load", "hofem_lift_dirichlet", "hofem_mass", "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders",
-    "hofem_apply_varcoef", "hofem_pcg",
+    "hofem_apply_varcoef", "hofem_pcg", "hofem_sweep", "hofem_copy_block",
 )
 
 
@@ -116,6 +116,9 @@ def load_library():
     lib.hofem_batch_get_plan.argtypes = [P, I, ctypes.POINTER(P)]
     lib.hofem_batch_partition.argtypes = [I, ctypes.POINTER(hofem_problem), I, I, ctypes.POINTER(I),
                                           ctypes.POINTER(D)]
+    LL = ctypes.c_longlong
+    lib.hofem_sweep.argtypes = [P, I, I, V, V, LL, LL, LL, V]
+    lib.hofem_copy_block.argtypes = [V, V, LL, LL, LL, LL, LL, LL, LL, V]
     lib.hofem_batch_destroy.argtypes = [P]
     lib.hofem_batch_destroy.restype = None
     for name in ("hofem_plan", "hofem_set_refinement", "hofem_reserve", "hofem_solve", "hofem_apply",
@@ -125,7 +128,7 @@ def load_library():
                  "hofem_batch_get_plan", "hofem_batch_partition", "hofem_quadrature_points", "hofem_load",
                  "hofem_lift_dirichlet", "hofem_mass",
                  "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders", "hofem_apply_varcoef",
-                 "hofem_pcg"):
+                 "hofem_pcg", "hofem_sweep", "hofem_copy_block"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -220,6 +223,22 @@ def hofem_transform1d(plan, axis, inverse, x, y, lines, stream=None):
                                             _stream(stream)), "hofem_transform1d")
 
 
+HOFEM_SWEEP_FORWARD, HOFEM_SWEEP_FUSED, HOFEM_SWEEP_INVERSE = 0, 1, 2
+
+
+def hofem_sweep(plan, axis, mode, x, y, outer, inner, line_offset=0, stream=None):
+    _check(load_library().hofem_sweep(plan, int(axis), int(mode), _ptr(x), _ptr(y), int(outer), int(inner),
+                                      int(line_offset), _stream(stream)), "hofem_sweep")
+
+
+def hofem_copy_block(src, dst, batch, rows, cols, src_ld, dst_ld, src_bs, dst_bs, stream=None):
+    """dst[b][r][c] = src[b][r][c] (element offsets b *_bs + r *_ld + c); src, dst: device
+    pointers or tensors (an int is an address, e.g. a tensor's data_ptr plus an offset)."""
+    _check(load_library().hofem_copy_block(_ptr(src), _ptr(dst), int(batch), int(rows), int(cols), int(src_ld),
+                                           int(dst_ld), int(src_bs), int(dst_bs), _stream(stream)),
+           "hofem_copy_block")
+
+
 def hofem_get_eigen(plan, axis):
     """Host copies (lam[M], mix[K-1, n, n], evec[n-1, n-1]) of one axis' eigen-data."""
     import numpy as np
@@ -280,6 +299,9 @@ class Plan:
 
     def transform1d(self, axis, inverse, x, y, lines, stream=None):
         hofem_transform1d(self.handle, axis, inverse, x, y, lines, stream)
+
+    def sweep(self, axis, mode, x, y, outer, inner, line_offset=0, stream=None):
+        hofem_sweep(self.handle, axis, mode, x, y, outer, inner, line_offset, stream)
 
     def set_refinement(self, iters, tol=0.0):
         hofem_set_refinement(self.handle, iters, tol)

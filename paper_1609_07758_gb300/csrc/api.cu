@@ -389,11 +389,14 @@ bool use_reg_sweep(const DevAxis& A, bool f64, int mode, bool strided, int in_fm
 hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void* in, int in_fmt, void* out,
                        int out_fmt, bool accumulate, double* norms, long long nrhs, cudaStream_t s,
                        long long lines_override = -1, const unsigned long long* in_amax = nullptr,
-                       const unsigned long long* out_amax = nullptr, int norm_slot = 0) {
+                       const unsigned long long* out_amax = nullptr, int norm_slot = 0,
+                       const Geo* block = nullptr, long long line_offset = 0) {
   const DevAxis& A = p->ax[axis];
   SweepParams P{};
   Geo g = geometry(p, axis);
   if (lines_override >= 0) g = Geo{lines_override, 1};
+  if (block) g = *block;   // a block of lines of its own geometry (nrhs is folded into it)
+  P.line_offset = line_offset;
   const int tsize = f64 ? 8 : 4;
   const bool strided = g.inner > 1;
   const long long lines = nrhs * g.outer_per_rhs * g.inner;
@@ -518,13 +521,15 @@ hofem_status run_sweep(hofem_plan_s* p, int axis, int mode, bool f64, const void
 // number; after the division rounding errors stay relative.  FP16 adds an exact
 // power-of-two scale of each right-hand side.
 hofem_status solve_once(hofem_plan_s* p, const double* f, double* u, int nrhs, bool f64, bool accumulate,
-                        double* norms, int norm_slot, cudaStream_t s) {
+                        double* norms, int norm_slot, cudaStream_t s, int f_fmt = kFmtF64) {
   hofem_status st;
   void* wa = f64 ? (void*)u : (void*)p->work32;                                   // before the division
   void* wb = f64 ? (void*)u : (p->wfmt == kFmtF32 ? (void*)p->work32 : p->work16);  // after it
   const int fa = f64 ? kFmtF64 : kFmtF32, fb = f64 ? kFmtF64 : p->wfmt;
   if (f64 && accumulate) return fail(HOFEM_ERR_INVALID_ARG, "internal: FP64 solve cannot accumulate");
   const unsigned long long* amax = nullptr;
+  if (f_fmt != kFmtF64 && (f64 || p->wfmt == kFmtF16))
+    return fail(HOFEM_ERR_INVALID_ARG, "internal: an FP32 right-hand side needs an FP32 or BF16 solve");
   if (!f64 && p->wfmt == kFmtF16) {
     HOFEM_CUDA(cudaMemsetAsync(p->amax, 0, (size_t)nrhs * sizeof(unsigned long long), s), "memset amax");
     HOFEM_CUDA(launch_absmax(f, p->total, nrhs, p->amax, s), "absmax launch");
@@ -532,7 +537,7 @@ hofem_status solve_once(hofem_plan_s* p, const double* f, double* u, int nrhs, b
   }
   const int N = p->N;
   // forward along the contiguous axis, then the strided ones down to axis 1
-  if ((st = run_sweep(p, N - 1, kFwd, f64, f, kFmtF64, wa, fa, false, nullptr, nrhs, s, -1, amax)) != HOFEM_OK)
+  if ((st = run_sweep(p, N - 1, kFwd, f64, f, f_fmt, wa, fa, false, nullptr, nrhs, s, -1, amax)) != HOFEM_OK)
     return st;
   for (int a = N - 2; a >= 1; --a)
     if ((st = run_sweep(p, a, kFwd, f64, wa, fa, wa, fa, false, nullptr, nrhs, s)) != HOFEM_OK) return st;
@@ -545,7 +550,8 @@ hofem_status solve_once(hofem_plan_s* p, const double* f, double* u, int nrhs, b
 // One operator sweep along `axis` (modes in residual.cuh): Q == nullptr is the first
 // sweep (out1 required), Q and out1 a middle one, Q without out1 the last one.
 hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double* Q_, double* out1, double* out2,
-                       const double* f, double cA, double cCP, int nrhs, cudaStream_t s, bool uniform = false) {
+                       const double* f, double cA, double cCP, int nrhs, cudaStream_t s, bool uniform = false,
+                       bool out_f32 = false) {
   const DevAxis& A = p->ax[axis];
   Geo g = geometry(p, axis);
   const bool strided = g.inner > 1;
@@ -592,6 +598,7 @@ hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double
   P.cA = cA * A.h.a_scale;
   P.cCP = cCP;
   P.uniform = uniform ? 1 : 0;
+  P.out2_f32 = out_f32 && P.mode == kApplyLast ? 1 : 0;
   std::copy(A.h.CfE.begin(), A.h.CfE.end(), P.CE);
   std::copy(A.h.CfO.begin(), A.h.CfO.end(), P.CO);
   std::copy(A.h.AfE.begin(), A.h.AfE.end(), P.AE);
@@ -616,9 +623,11 @@ bool uniform_stiffness(const hofem_plan_s* p, const double* sc) {
   return c0 != 0.0;
 }
 
-// out = A u (f == nullptr) or out = f - A u, Eq. bvp glob 2, by one sweep per axis.
+// out = A u (f == nullptr) or out = f - A u, Eq. bvp glob 2, by one sweep per axis; with
+// out_f32 the result is written as FP32 values into out's memory (a correction's FP32 solve
+// rounds it to FP32 on reading anyway).
 hofem_status operator_apply(hofem_plan_s* p, const double* u, const double* f, double* out, int nrhs,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool out_f32 = false) {
   hofem_status st = reserve(p, nrhs);
   if (st != HOFEM_OK) return st;
   const int N = p->N;
@@ -630,21 +639,21 @@ hofem_status operator_apply(hofem_plan_s* p, const double* u, const double* f, d
     const double c = sc[0] * p->ax[0].h.a_scale, ac = p->alpha / c;
     if (N == 2) {
       if ((st = run_apply(p, 1, u, nullptr, t[0], t[1], nullptr, sc[1], ac, nrhs, s, true)) != HOFEM_OK) return st;
-      return run_apply(p, 0, t[0], t[1], nullptr, out, f, sc[0], 0.0, nrhs, s, true);
+      return run_apply(p, 0, t[0], t[1], nullptr, out, f, sc[0], 0.0, nrhs, s, true, out_f32);
     }
     if ((st = run_apply(p, 2, u, nullptr, t[0], t[1], nullptr, sc[2], ac, nrhs, s, true)) != HOFEM_OK) return st;
     if ((st = run_apply(p, 1, t[0], t[1], t[2], t[3], nullptr, sc[1], 0.0, nrhs, s, true)) != HOFEM_OK) return st;
-    return run_apply(p, 0, t[2], t[3], nullptr, out, f, sc[0], 0.0, nrhs, s, true);
+    return run_apply(p, 0, t[2], t[3], nullptr, out, f, sc[0], 0.0, nrhs, s, true, out_f32);
   }
   if (N == 2) {
     // axis 1: T1 = u xC, T2 = s1 (u xA) + alpha (u xC); axis 0: out = [f -] (s0 T1 xA + T2 xC)
     if ((st = run_apply(p, 1, u, nullptr, t[0], t[1], nullptr, sc[1], p->alpha, nrhs, s)) != HOFEM_OK) return st;
-    return run_apply(p, 0, t[0], t[1], nullptr, out, f, sc[0], 0.0, nrhs, s);
+    return run_apply(p, 0, t[0], t[1], nullptr, out, f, sc[0], 0.0, nrhs, s, false, out_f32);
   }
   // N == 3
   if ((st = run_apply(p, 2, u, nullptr, t[0], t[1], nullptr, sc[2], p->alpha, nrhs, s)) != HOFEM_OK) return st;
   if ((st = run_apply(p, 1, t[0], t[1], t[2], t[3], nullptr, sc[1], 0.0, nrhs, s)) != HOFEM_OK) return st;
-  return run_apply(p, 0, t[2], t[3], nullptr, out, f, sc[0], 0.0, nrhs, s);
+  return run_apply(p, 0, t[2], t[3], nullptr, out, f, sc[0], 0.0, nrhs, s, false, out_f32);
 }
 
 
@@ -1416,10 +1425,15 @@ hofem_status hofem_solve(hofem_plan_t p, const double* f, double* u, int nrhs, v
   if ((st = solve_once(p, f, u, nrhs, false, false, iters > 0 ? p->norms : nullptr, 1, s)) != HOFEM_OK) return st;
   int done = 0;
   bool converged = false;
+  // an FP32 correction solve reads its right-hand side as FP32 values: the residual is
+  // written that way (into the residual buffer), which halves its store and the first
+  // sweep's load and lets that sweep use the asynchronous FP32 tile path
+  const bool r32 = p->wfmt == kFmtF32;
   for (int i = 0; i < iters; ++i) {
-    if ((st = operator_apply(p, u, f, p->r64, nrhs, s)) != HOFEM_OK) return st;
+    if ((st = operator_apply(p, u, f, p->r64, nrhs, s, r32)) != HOFEM_OK) return st;
     HOFEM_CUDA(cudaMemset2DAsync(p->norms, 2 * sizeof(double), 0, sizeof(double), nrhs, s), "memset norms");
-    if ((st = solve_once(p, p->r64, u, nrhs, false, true, p->norms, 0, s)) != HOFEM_OK) return st;
+    if ((st = solve_once(p, p->r64, u, nrhs, false, true, p->norms, 0, s, r32 ? kFmtF32 : kFmtF64)) != HOFEM_OK)
+      return st;
     ++done;
     if (adaptive) {
       HOFEM_CUDA(cudaMemcpyAsync(p->h_norms, p->norms, 2 * (size_t)nrhs * sizeof(double), cudaMemcpyDeviceToHost, s),
@@ -1476,6 +1490,36 @@ hofem_status hofem_transform1d(hofem_plan_t p, int axis, int inverse, const doub
   // work in the output buffer: FP64 in place, or via the FP32 path converting on load/store
   return run_sweep(p, axis, inverse ? kInv : kFwd, f64, in, kFmtF64, out, kFmtF64, false, nullptr, 1,
                    (cudaStream_t)stream, lines);
+}
+
+hofem_status hofem_sweep(hofem_plan_t p, int axis, int mode, const double* in, double* out, long long outer,
+                         long long inner, long long line_offset, void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  if (axis < 0 || axis >= p->N) return fail(HOFEM_ERR_INVALID_ARG, "axis out of range");
+  if (!in || !out || outer < 0 || inner < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or block sizes");
+  if (mode < HOFEM_SWEEP_FORWARD || mode > HOFEM_SWEEP_INVERSE) return fail(HOFEM_ERR_INVALID_ARG, "bad mode");
+  if (p->dtype != HOFEM_FP64 && p->dtype != HOFEM_FP32)
+    return fail(HOFEM_ERR_UNSUPPORTED, "block sweeps run in FP64 or FP32 (unrefined) plans");
+  long long plane = 1;
+  for (int i = 1; i < p->N; ++i) plane *= p->M[i];
+  if (mode == HOFEM_SWEEP_FUSED && (axis != 0 || line_offset < 0 || line_offset + inner > plane))
+    return fail(HOFEM_ERR_INVALID_ARG, "the fused sweep runs along axis 0 on columns inside the x_2..x_N plane");
+  if (outer == 0) return HOFEM_OK;
+  const int m = mode == HOFEM_SWEEP_FORWARD ? kFwd : mode == HOFEM_SWEEP_FUSED ? kFwdScaleInv : kInv;
+  const Geo block{outer, inner};
+  return run_sweep(p, axis, m, p->dtype == HOFEM_FP64, in, kFmtF64, out, kFmtF64, false, nullptr, 1,
+                   (cudaStream_t)stream, -1, nullptr, nullptr, 0, &block, mode == HOFEM_SWEEP_FUSED ? line_offset : 0);
+}
+
+hofem_status hofem_copy_block(const double* src, double* dst, long long batch, long long rows, long long cols,
+                              long long src_ld, long long dst_ld, long long src_bs, long long dst_bs, void* stream) {
+  if (batch < 0 || rows < 0 || cols < 0) return fail(HOFEM_ERR_INVALID_ARG, "negative block sizes");
+  if (batch * rows * cols == 0) return HOFEM_OK;
+  if (!src || !dst || src_ld < cols || dst_ld < cols || (batch > 1 && (src_bs < rows * src_ld || dst_bs < rows * dst_ld)))
+    return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or leading dimensions");
+  HOFEM_CUDA(launch_copy_block(src, dst, batch, rows, cols, src_ld, dst_ld, src_bs, dst_bs, (cudaStream_t)stream),
+             "copy_block launch");
+  return HOFEM_OK;
 }
 
 hofem_status hofem_get_eigen(hofem_plan_t p, int axis, double* lam, double* mix, double* evec) {

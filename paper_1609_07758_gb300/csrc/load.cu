@@ -64,7 +64,28 @@ __global__ void axpy_kernel(double* __restrict__ y, double c, const double* __re
     y[i] = fma(c, __ldg(x + i), y[i]);
 }
 
+// dst[b][r][c] = src[b][r][c] for a batch of row blocks with their own leading dimensions
+__global__ void copy_block_kernel(const double* __restrict__ src, double* __restrict__ dst, long long batch,
+                                  long long rows, long long cols, long long src_ld, long long dst_ld,
+                                  long long src_bs, long long dst_bs) {
+  const long long total = batch * rows * cols;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long c = i % cols, t = i / cols, r = t % rows, b = t / rows;
+    dst[b * dst_bs + r * dst_ld + c] = __ldg(src + b * src_bs + r * src_ld + c);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_copy_block(const double* src, double* dst, long long batch, long long rows, long long cols,
+                              long long src_ld, long long dst_ld, long long src_bs, long long dst_bs,
+                              cudaStream_t s) {
+  const long long total = batch * rows * cols;
+  if (total <= 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 16);
+  copy_block_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, dst, batch, rows, cols, src_ld, dst_ld, src_bs, dst_bs);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_axpy(double* y, double c, const double* x, long long count, cudaStream_t s) {
   const long long blocks = std::min<long long>((count + 255) / 256, 152LL * 16);

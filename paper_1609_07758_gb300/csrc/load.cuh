@@ -19,5 +19,9 @@ cudaError_t launch_load(const LoadParams& p, cudaStream_t s);
 cudaError_t launch_axpby(double* y, double a, const double* g, long long count, cudaStream_t s);
 // y += c x
 cudaError_t launch_axpy(double* y, double c, const double* x, long long count, cudaStream_t s);
+// dst[b][r][c] = src[b][r][c], b < batch, r < rows, c < cols (leading dimensions per side)
+cudaError_t launch_copy_block(const double* src, double* dst, long long batch, long long rows, long long cols,
+                              long long src_ld, long long dst_ld, long long src_bs, long long dst_bs,
+                              cudaStream_t s);
 
 }  // namespace hofem

@@ -29,6 +29,7 @@
 // multiply per output row of the first sweep and one combining operation per row of the
 // later ones.
 #include "common.cuh"
+#include "convert.cuh"
 #include "residual.cuh"
 
 namespace hofem {
@@ -256,7 +257,8 @@ __global__ void __launch_bounds__(kApplyThreads, N <= kApplyMinb3MaxN ? 3 : N <=
         if (US) v = use_f ? fma(-P.cA, v, fv[u]) : P.cA * v;
         else if (use_f) v = fv[u] - v;
       }
-      P.out2[gg[u]] = v;
+      if (MODE == kApplyLast && P.out2_f32) reinterpret_cast<float*>(P.out2)[gg[u]] = f64_to_f32_bits(v);
+      else P.out2[gg[u]] = v;
       if (PC) P.out1[gg[u]] = tP[(size_t)rr[u] * kLd + ww[u]];
     }
   }

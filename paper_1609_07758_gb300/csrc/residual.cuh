@@ -31,6 +31,8 @@ struct ApplyParams {
   int mode;                                // ApplyMode
   int uniform;                             // every axis has the same stiffness coefficient:
                                            // out2 unscaled, cA applied by the last sweep
+  int out2_f32;                            // kApplyLast: out2 is an FP32 array (the right-hand
+                                           // side of an FP32 correction solve)
   const double* P;
   const double* Q;                         // kApplyMid, kApplyLast
   double* out1;                            // kApplyFirst, kApplyMid

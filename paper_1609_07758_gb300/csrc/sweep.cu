@@ -1117,7 +1117,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? HOFEM_F32_THREADS : 512, 1) s
   }
   if (P.mode == kFwdScaleInv) {
     for (int w = threadIdx.x; w < W; w += blockDim.x) {
-      const long long c = l0 + w;
+      const long long c = P.line_offset + l0 + w;
       double rest = 0.0;
       if (w < wvalid) {
         const long long qa = P.lamB ? c / P.MB : c;

@@ -64,6 +64,8 @@ struct SweepParams {
   const void* lamA;           // lam_rest(c) = lamA[c / MB] + lamB[c % MB] (lamB may be null)
   const void* lamB;
   long long MB;
+  long long line_offset;      // index of the sweep's first line among the columns c (a block
+                              // of columns of a problem split over several GPUs; else 0)
   double alpha;
   // FFT plan for length K: radices of the DIF passes (first pass first); pow2 = 1 for
   // K = 2^m (in-place register passes), else out-of-place mixed-radix passes, whose

@@ -32,9 +32,7 @@
 #ifndef HOFEM_REG_MIX
 #define HOFEM_REG_MIX 0
 #endif
-#if HOFEM_REG_PART == 100
-#pragma nv_diag_suppress 177   // the table part uses only some members of the shape structs
-#endif
+#pragma nv_diag_suppress 177   // each part compiles one kernel and uses only some helpers
 
 namespace hofem {
 namespace {
@@ -122,6 +120,7 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, int src_
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+
 
 template <int R> __host__ __device__ constexpr int brev(int i) {
   int o = 0;
@@ -520,88 +519,119 @@ __device__ __forceinline__ void mixing(float* tile, float* save, const float* lr
   __syncthreads();
 }
 
-// One tile (W lines) of a sweep of MODE (kFwd, kFwdScaleInv or kInv) over contiguous
-// (CONTIG) or strided lines.
-template <int N, int LOGK, int W, int NW, int MINB, int MODE, bool CONTIG>
-__device__ __forceinline__ void reg_tile(const SweepParams& P, const long long b, unsigned char* smem_raw) {
-  using C = RegCfg<N, LOGK, W, NW>;
-  constexpr int M = C::M, MS = C::MS, NT = C::NT, K = C::K;
-  static_assert((W & (W - 1)) == 0, "W is a power of two");
-  constexpr int LW = W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : W == 16 ? 4 : 5;
-  float* tile = reinterpret_cast<float*>(smem_raw);
-  float* scr = tile + C::TF;
-  float* save = scr + C::SCR;
-  const float2* twx = (const float2*)P.twr;
-  const float2* twz = twx + K;
-  float* lrest = save + C::SAVE;
-  double* red = reinterpret_cast<double*>(lrest + C::LR);
-  const int tid = threadIdx.x;
+// Where tile b of a sweep lies: outer index o, first line l0, lines present, right-hand
+// side and the global offset of its first element.
+struct TileGeo {
+  long long o, l0, rhs, gbase;
+  int wvalid;
+};
 
-  const long long o = b / P.tiles_per_outer, tix = b - o * P.tiles_per_outer;
-  const long long l0 = tix * W;
+template <int W, int M, bool CONTIG>
+__device__ __forceinline__ TileGeo tile_geo(const SweepParams& P, const long long b) {
+  TileGeo g;
+  g.o = b / P.tiles_per_outer;
+  const long long tix = b - g.o * P.tiles_per_outer;
+  g.l0 = tix * W;
   const long long nl = CONTIG ? P.outer_per_rhs : P.inner;
-  const int wvalid = (int)(nl - l0 < W ? nl - l0 : W);
-  const long long rhs = CONTIG ? o : o / P.outer_per_rhs;
-  const long long gbase = CONTIG ? (o * P.outer_per_rhs + l0) * (long long)M : o * (long long)M * P.inner + l0;
-  const long long inner = P.inner;
+  g.wvalid = (int)(nl - g.l0 < W ? nl - g.l0 : W);
+  g.rhs = CONTIG ? g.o : g.o / P.outer_per_rhs;
+  g.gbase = CONTIG ? (g.o * P.outer_per_rhs + g.l0) * (long long)M : g.o * (long long)M * P.inner + g.l0;
+  return g;
+}
 
-  // ---- load W lines (missing lines read as zeros).  Contiguous lines go line by line
-  // (position p = p0 + u NT, no index division); strided tiles as elements e = p W + w.
-  // The loads of an unrolled group are unconditional at clamped valid addresses, so that
-  // they are all in flight at once.
-  constexpr int TOT = W * M, U = 16, UL = 32;
-  if (P.in_fmt == kFmtF64) {
-    const double* __restrict__ in = (const double*)P.in;
-    if constexpr (CONTIG) {
-      for (int w = 0; w < W; ++w) {
-        const bool lv = w < wvalid;
-        const double* src = in + gbase + (long long)(lv ? w : 0) * M;
-        for (int p0 = tid; p0 < M; p0 += UL * NT) {
-          double v[UL];
-#pragma unroll
-          for (int u = 0; u < UL; ++u) v[u] = __ldg(src + (p0 + u * NT < M ? p0 + u * NT : 0));
-#pragma unroll
-          for (int u = 0; u < UL; ++u)
-            if (p0 + u * NT < M) tile[w * MS + p0 + u * NT] = lv ? (float)v[u] : 0.f;
-        }
-      }
-    } else {
-      for (int e0 = tid; e0 < TOT; e0 += UL * NT) {
+// Load W FP64 lines into the FP32 tile (missing lines read as zeros).  Contiguous lines go
+// line by line (position p = p0 + u NT, no index division); strided tiles as elements
+// e = p W + w.  The loads of an unrolled group are unconditional at clamped valid
+// addresses, so that they are all in flight at once.
+template <class C, bool CONTIG>
+__device__ __forceinline__ void load_f64(const SweepParams& P, const TileGeo& g, float* tile) {
+  constexpr int M = C::M, MS = C::MS, NT = C::NT, W = C::W, TOT = W * M, UL = 32;
+  constexpr int LW = W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : W == 16 ? 4 : 5;
+  const int tid = threadIdx.x;
+  const double* __restrict__ in = (const double*)P.in;
+  if constexpr (CONTIG) {
+    for (int w = 0; w < W; ++w) {
+      const bool lv = w < g.wvalid;
+      const double* src = in + g.gbase + (long long)(lv ? w : 0) * M;
+      for (int p0 = tid; p0 < M; p0 += UL * NT) {
         double v[UL];
 #pragma unroll
-        for (int u = 0; u < UL; ++u) {
-          const int e = e0 + u * NT, w = e & (W - 1), p = e >> LW;
-          v[u] = __ldg(in + ((e < TOT && w < wvalid) ? gbase + p * inner + w : gbase));
-        }
+        for (int u = 0; u < UL; ++u) v[u] = __ldg(src + (p0 + u * NT < M ? p0 + u * NT : 0));
 #pragma unroll
-        for (int u = 0; u < UL; ++u) {
-          const int e = e0 + u * NT, w = e & (W - 1), p = e >> LW;
-          if (e < TOT) tile[w * MS + p] = w < wvalid ? (float)v[u] : 0.f;
-        }
+        for (int u = 0; u < UL; ++u)
+          if (p0 + u * NT < M) tile[w * MS + p0 + u * NT] = lv ? (float)v[u] : 0.f;
       }
     }
   } else {
-    // FP32 input: asynchronous 4-byte copies straight into the tile (zero-filled for the
-    // missing lines), the whole tile in flight at once
-    const float* __restrict__ in = (const float*)P.in;
-    if constexpr (CONTIG) {
-      for (int w = 0; w < W; ++w) {
-        const bool lv = w < wvalid;
-        const float* src = in + gbase + (long long)(lv ? w : 0) * M;
-        for (int p = tid; p < M; p += NT) cp_async4(tile + w * MS + p, src + p, lv ? 4 : 0);
+    for (int e0 = tid; e0 < TOT; e0 += UL * NT) {
+      double v[UL];
+#pragma unroll
+      for (int u = 0; u < UL; ++u) {
+        const int e = e0 + u * NT, w = e & (W - 1), p = e >> LW;
+        v[u] = __ldg(in + ((e < TOT && w < g.wvalid) ? g.gbase + p * P.inner + w : g.gbase));
       }
-    } else {
-      for (int e = tid; e < TOT; e += NT) {
-        const int w = e & (W - 1), p = e >> LW;
-        const bool ok = w < wvalid;
-        cp_async4(tile + w * MS + p, in + (ok ? gbase + p * inner + w : gbase), ok ? 4 : 0);
+#pragma unroll
+      for (int u = 0; u < UL; ++u) {
+        const int e = e0 + u * NT, w = e & (W - 1), p = e >> LW;
+        if (e < TOT) tile[w * MS + p] = w < g.wvalid ? (float)v[u] : 0.f;
       }
     }
-    cp_async_wait_all();
   }
+}
+
+// Issue asynchronous 4-byte copies of W FP32 lines straight into the tile (zero-filled for
+// the missing lines), the whole tile in flight at once; the caller commits and waits.
+template <class C, bool CONTIG>
+__device__ __forceinline__ void load_f32_async(const SweepParams& P, const TileGeo& g, float* tile) {
+  constexpr int M = C::M, MS = C::MS, NT = C::NT, W = C::W, TOT = W * M;
+  constexpr int LW = W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : W == 16 ? 4 : 5;
+  const int tid = threadIdx.x;
+  const float* __restrict__ in = (const float*)P.in;
+  if constexpr (CONTIG) {
+    for (int w = 0; w < W; ++w) {
+      const bool lv = w < g.wvalid;
+      const float* src = in + g.gbase + (long long)(lv ? w : 0) * M;
+      for (int p = tid; p < M; p += NT) cp_async4(tile + w * MS + p, src + p, lv ? 4 : 0);
+    }
+  } else {
+    for (int e = tid; e < TOT; e += NT) {
+      const int w = e & (W - 1), p = e >> LW;
+      const bool ok = w < g.wvalid;
+      cp_async4(tile + w * MS + p, in + (ok ? g.gbase + p * P.inner + w : g.gbase), ok ? 4 : 0);
+    }
+  }
+}
+
+// Shared-memory areas of a CTA besides its tile(s).
+struct RegAreas {
+  float* scr;
+  float* save;
+  float* lrest;
+  double* red;
+};
+
+// Everything of tile g after its load has been issued and completed by this thread: the
+// per-line eigenvalue rest of the fused sweep, a barrier (the tile and rests visible to all),
+// the transforms and mixing, the store (and the norm of the stored update).
+template <class C, int MODE, bool CONTIG>
+__device__ __forceinline__ void work_tile(const SweepParams& P, const TileGeo& g, float* tile, const RegAreas& a) {
+  constexpr int N = C::N, W = C::W, NW = C::NW;
+  constexpr int M = C::M, MS = C::MS, NT = C::NT, K = C::K;
+  static_assert((W & (W - 1)) == 0, "W is a power of two");
+  constexpr int LW = W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : W == 16 ? 4 : 5;
+  constexpr int TOT = W * M, U = 16;
+  float* scr = a.scr;
+  float* save = a.save;
+  float* lrest = a.lrest;
+  double* red = a.red;
+  const float2* twx = (const float2*)P.twr;
+  const float2* twz = twx + K;
+  const int tid = threadIdx.x;
+  const long long l0 = g.l0, rhs = g.rhs, gbase = g.gbase, inner = P.inner;
+  const int wvalid = g.wvalid;
   if constexpr (MODE == kFwdScaleInv) {
     for (int w = tid; w < W; w += NT) {
-      const long long c = l0 + w;
+      const long long c = P.line_offset + l0 + w;
       float rest = 0.f;
       if (w < wvalid) {
         const long long qa = P.lamB ? c / P.MB : c;
@@ -733,8 +763,21 @@ __device__ __forceinline__ void reg_tile(const SweepParams& P, const long long b
 // One sweep of MODE over contiguous (CONTIG) or strided lines: one CTA per tile of W lines.
 template <int N, int LOGK, int W, int NW, int MINB, int MODE, bool CONTIG>
 __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepParams P) {
+  using C = RegCfg<N, LOGK, W, NW>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  reg_tile<N, LOGK, W, NW, MINB, MODE, CONTIG>(P, blockIdx.x, smem_raw);
+  float* tile = reinterpret_cast<float*>(smem_raw);
+  float* scr = tile + C::TF;
+  float* save = scr + C::SCR;
+  float* lrest = save + C::SAVE;
+  const RegAreas a{scr, save, lrest, reinterpret_cast<double*>(lrest + C::LR)};
+  const TileGeo g = tile_geo<W, C::M, CONTIG>(P, blockIdx.x);
+  if (P.in_fmt == kFmtF64) {
+    load_f64<C, CONTIG>(P, g, tile);
+  } else {
+    load_f32_async<C, CONTIG>(P, g, tile);
+    cp_async_wait_all();
+  }
+  work_tile<C, MODE, CONTIG>(P, g, tile, a);
 }
 
 }  // namespace
@@ -766,6 +809,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) sweep_reg_kernel(const SweepPar
   HOFEM_REG_CALL(X, 0, HOFEM_REG_SHAPE0) \
   HOFEM_REG_CALL(X, 1, HOFEM_REG_SHAPE1) \
   HOFEM_REG_CALL(X, 2, HOFEM_REG_SHAPE2)
+
 
 #define HOFEM_REG_DECL(ID, NN, LK, WW, NWW, MB)                                                \
   cudaError_t reg_attr_##ID##_0(); cudaError_t reg_attr_##ID##_1(); cudaError_t reg_attr_##ID##_2(); \
