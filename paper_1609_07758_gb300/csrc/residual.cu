@@ -103,7 +103,8 @@ __device__ __forceinline__ void element_rows(const ApplyParams& P, double* tP, d
       qa = cq[t * kLd];
       qc = cq[(n - t) * kLd];
     }
-    column(t, false, a + c, a - c, t == 0 ? c - w0 : (a - w0) + (c - w0), qa + qc, qa - qc);
+    // t = 0: a is w0 itself, so the difference c - w0 is exactly -(a - c), the odd part
+    column(t, false, a + c, a - c, t == 0 ? -(a - c) : (a - w0) + (c - w0), qa + qc, qa - qc);
   }
   if (has_mid) {
     const double a = cp[(n / 2) * kLd];
