@@ -535,14 +535,15 @@ def main():
     # algorithmic work per launch (per unknown x unknowns): one operator sweep applies two
     # folded element matrices, 2 (h_even^2 + h_odd^2) flops each per element and line
     fp64_flops_apply = 2 * 2 * (h_even ** 2 + h_odd ** 2) / N_ORDER * UNKNOWNS
-    # bytes per unknown of each sweep of the FP32-refined path: forward reads FP64, writes FP32;
-    # fused reads and writes FP32; inverse reads FP32 and, in the corrections, the FP64 u it
-    # accumulates into, and writes u (12 B in the first solve of a step, which only writes u)
+    # bytes per unknown of each sweep of the FP32-refined path: forward reads FP64 f and writes
+    # FP32 (12 B) in the first solve of a step, and reads the FP32 residual (8 B) in the
+    # corrections; fused reads and writes FP32; inverse reads FP32 and, in the corrections, the
+    # FP64 u it accumulates into, and writes u (12 B in the first solve, which only writes u)
     solves = kinds.get("sweep_inv_reg", kinds.get("sweep_inv_f32", {"launches": 0}))["launches"]
     first = solves / (args.refine_iters + 1) if solves else 0
     def sweep_bytes(kind, launches):
         if kind.startswith("sweep_fwd"):
-            return 12.0 * launches * UNKNOWNS
+            return (12.0 * first + 8.0 * (launches - first)) * UNKNOWNS
         if kind.startswith("sweep_fsi"):
             return 8.0 * launches * UNKNOWNS
         return (20.0 * (launches - first) + 12.0 * first) * UNKNOWNS
