@@ -298,11 +298,33 @@ enum { HOFEM_SWEEP_FORWARD = 0, HOFEM_SWEEP_FUSED = 1, HOFEM_SWEEP_INVERSE = 2 }
  *     column c = line_offset + l indexes the x_2..x_N plane in C order (c = q_2 for N = 2,
  *     c = q_2 M_3 + q_3 for N = 3), then the inverse transform.  line_offset + inner must
  *     not exceed the plane's size; nrhs > 1 is outer = nrhs with the same columns.
- * Runs in the plan's precision: FP64 plans in FP64, FP32 (unrefined) plans in FP32
- * arithmetic with FP64 input and output; other dtypes return HOFEM_ERR_UNSUPPORTED.
- * Asynchronous on stream. */
+ * FP64 plans run it in FP64; every other dtype in FP32 arithmetic (a refined plan's correction
+ * sweeps) with FP64 input and output.  Asynchronous on stream. */
 hofem_status hofem_sweep(hofem_plan_t plan, int axis, int mode, const double* in, double* out,
                          long long outer, long long inner, long long line_offset, void* stream);
+
+/* The FP64 residual r = f - A u (Eq. bvp glob 2, as hofem_residual) of one slab of a problem
+ * split over GPUs by x_1: the slab owns elements e0 .. e1 - 1 along x_1, i.e. the dof rows
+ * e0 n .. min(e1 n, M_1) - 1 ("rows"), with every x_2..x_N index.  Two stages with an exchange
+ * of halo rows between them:
+ *   stage 0: a = u of the slab, [nrhs][rows][M_2..M_N]; the operator's sweeps along x_N .. x_2
+ *     write its two intermediate arrays out0, out1, laid out [nrhs][ext][M_2..M_N] with
+ *     ext = pre + rows + post (pre = 1 if e0 > 0, post = n if e1 < K_1), into rows
+ *     pre .. pre + rows - 1.  The caller then fills row 0 (when pre = 1) with the previous
+ *     slab's last row and the last `post` rows with the next slab's first n rows, of both
+ *     arrays.
+ *   stage 1: a, b = the filled intermediates; the sweep along x_1 over the slab's elements
+ *     writes out0 = f - A u on the slab's rows, [nrhs][rows][M_2..M_N], FP64 or, with
+ *     out_fp32, FP32 values (f: [nrhs][rows][..] FP64, may be NULL for out0 = A u).
+ * All device pointers; b, f, out1 unused where not named.  The stage-0 scratch of a 3D plan
+ * is the plan's workspace (reserved on first use).  Asynchronous on stream. */
+hofem_status hofem_residual_slab(hofem_plan_t plan, int stage, long long e0, long long e1, const double* a,
+                                 const double* b, const double* f, double* out0, double* out1, int out_fp32,
+                                 int nrhs, void* stream);
+
+/* y += c x over count FP64 values (device pointers; the correction u += delta of a refined
+ * solve driven from outside the library, e.g. over several GPUs).  Asynchronous on stream. */
+hofem_status hofem_axpy(double* y, double c, const double* x, long long count, void* stream);
 
 /* dst[b][r][c] = src[b][r][c] for b < batch, r < rows, c < cols, with element offsets
  * b src_bs + r src_ld + c (and the dst_* ones): the packing and unpacking of the blocks an

@@ -26,7 +26,8 @@ EXPORTED = (
     "hofem_batch_get_info", "hofem_batch_get_plan", "hofem_batch_destroy", "hofem_batch_partition",
     "hofem_quadrature_points",
     "hofem_load", "hofem_lift_dirichlet", "hofem_mass", "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders",
-    "hofem_apply_varcoef", "hofem_pcg", "hofem_sweep", "hofem_copy_block",
+    "hofem_apply_varcoef", "hofem_pcg", "hofem_sweep", "hofem_copy_block", "hofem_residual_slab",
+    "hofem_axpy",
 )
 
 
@@ -119,6 +120,8 @@ def load_library():
     LL = ctypes.c_longlong
     lib.hofem_sweep.argtypes = [P, I, I, V, V, LL, LL, LL, V]
     lib.hofem_copy_block.argtypes = [V, V, LL, LL, LL, LL, LL, LL, LL, V]
+    lib.hofem_residual_slab.argtypes = [P, I, LL, LL, V, V, V, V, V, I, I, V]
+    lib.hofem_axpy.argtypes = [V, D, V, LL, V]
     lib.hofem_batch_destroy.argtypes = [P]
     lib.hofem_batch_destroy.restype = None
     for name in ("hofem_plan", "hofem_set_refinement", "hofem_reserve", "hofem_solve", "hofem_apply",
@@ -128,7 +131,7 @@ def load_library():
                  "hofem_batch_get_plan", "hofem_batch_partition", "hofem_quadrature_points", "hofem_load",
                  "hofem_lift_dirichlet", "hofem_mass",
                  "hofem_heat_steps", "hofem_solve_banded", "hofem_plan_orders", "hofem_apply_varcoef",
-                 "hofem_pcg", "hofem_sweep", "hofem_copy_block"):
+                 "hofem_pcg", "hofem_sweep", "hofem_copy_block", "hofem_residual_slab", "hofem_axpy"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -229,6 +232,16 @@ HOFEM_SWEEP_FORWARD, HOFEM_SWEEP_FUSED, HOFEM_SWEEP_INVERSE = 0, 1, 2
 def hofem_sweep(plan, axis, mode, x, y, outer, inner, line_offset=0, stream=None):
     _check(load_library().hofem_sweep(plan, int(axis), int(mode), _ptr(x), _ptr(y), int(outer), int(inner),
                                       int(line_offset), _stream(stream)), "hofem_sweep")
+
+
+def hofem_residual_slab(plan, stage, e0, e1, a, b, f, out0, out1, out_fp32, nrhs, stream=None):
+    _check(load_library().hofem_residual_slab(plan, int(stage), int(e0), int(e1), _ptr(a), _ptr(b), _ptr(f),
+                                              _ptr(out0), _ptr(out1), int(out_fp32), int(nrhs), _stream(stream)),
+           "hofem_residual_slab")
+
+
+def hofem_axpy(y, c, x, count, stream=None):
+    _check(load_library().hofem_axpy(_ptr(y), float(c), _ptr(x), int(count), _stream(stream)), "hofem_axpy")
 
 
 def hofem_copy_block(src, dst, batch, rows, cols, src_ld, dst_ld, src_bs, dst_bs, stream=None):

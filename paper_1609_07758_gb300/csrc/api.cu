@@ -549,11 +549,21 @@ hofem_status solve_once(hofem_plan_s* p, const double* f, double* u, int nrhs, b
 
 // One operator sweep along `axis` (modes in residual.cuh): Q == nullptr is the first
 // sweep (out1 required), Q and out1 a middle one, Q without out1 the last one.
+// Lines of an operator sweep that are not the plan's grid: the block's geometry (one right-
+// hand side's outer lines and inner stride) and, when elems > 0, a stretch of the sweep's
+// axis -- input rows from global dof q0 (in_rows of them), output rows from dof out0
+// (out_rows), elements e0 .. e0 + elems - 1 (a slab of x_1 rows with its halo rows).
+struct ApplyBlock {
+  Geo g;
+  long long q0 = 0, in_rows = 0, e0 = 0, elems = 0, out0 = 0, out_rows = 0;
+};
+
 hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double* Q_, double* out1, double* out2,
                        const double* f, double cA, double cCP, int nrhs, cudaStream_t s, bool uniform = false,
-                       bool out_f32 = false) {
+                       bool out_f32 = false, const ApplyBlock* blk = nullptr) {
   const DevAxis& A = p->ax[axis];
-  Geo g = geometry(p, axis);
+  Geo g = blk ? blk->g : geometry(p, axis);
+  const bool part = blk && blk->elems > 0;   // a stretch of the axis, not whole lines
   const bool strided = g.inner > 1;
   ApplyParams P{};
   const int W = kApplyLines;
@@ -574,7 +584,7 @@ hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double
     if (e >= 1 && e <= 256) E = e;
   }
   while (apply_smem_bytes(A.h.n, E) > kSmemLimit && E > 1) E /= 2;
-  E = std::min(E, A.h.K);
+  E = std::min<long long>(E, part ? blk->elems : A.h.K);
   P.mode = Q_ == nullptr ? kApplyFirst : (out1 != nullptr ? kApplyMid : kApplyLast);
   if ((P.mode != kApplyLast) != (out1 != nullptr) || (P.mode == kApplyLast && cCP != 0.0) ||
       (P.mode != kApplyLast && f != nullptr))
@@ -583,7 +593,12 @@ hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double
   P.inner = g.inner;
   P.outer_per_rhs = g.outer_per_rhs;
   P.tiles_per_outer = strided ? (g.inner + W - 1) / W : (g.outer_per_rhs + W - 1) / W;
-  P.seg_per_line = (A.h.K + E - 1) / E;
+  P.seg_per_line = ((part ? blk->elems : A.h.K) + E - 1) / E;
+  P.blk_q0 = part ? blk->q0 : 0;
+  P.blk_in_rows = part ? blk->in_rows : A.h.M;
+  P.blk_e0 = part ? blk->e0 : 0;
+  P.blk_out0 = part ? blk->out0 : 0;
+  P.blk_out_rows = part ? blk->out_rows : A.h.M;
   P.ntiles = (strided ? P.outer : nrhs) * P.tiles_per_outer * P.seg_per_line;
   P.M = A.h.M;
   P.n = A.h.n;
@@ -1498,8 +1513,6 @@ hofem_status hofem_sweep(hofem_plan_t p, int axis, int mode, const double* in, d
   if (axis < 0 || axis >= p->N) return fail(HOFEM_ERR_INVALID_ARG, "axis out of range");
   if (!in || !out || outer < 0 || inner < 1) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or block sizes");
   if (mode < HOFEM_SWEEP_FORWARD || mode > HOFEM_SWEEP_INVERSE) return fail(HOFEM_ERR_INVALID_ARG, "bad mode");
-  if (p->dtype != HOFEM_FP64 && p->dtype != HOFEM_FP32)
-    return fail(HOFEM_ERR_UNSUPPORTED, "block sweeps run in FP64 or FP32 (unrefined) plans");
   long long plane = 1;
   for (int i = 1; i < p->N; ++i) plane *= p->M[i];
   if (mode == HOFEM_SWEEP_FUSED && (axis != 0 || line_offset < 0 || line_offset + inner > plane))
@@ -1509,6 +1522,69 @@ hofem_status hofem_sweep(hofem_plan_t p, int axis, int mode, const double* in, d
   const Geo block{outer, inner};
   return run_sweep(p, axis, m, p->dtype == HOFEM_FP64, in, kFmtF64, out, kFmtF64, false, nullptr, 1,
                    (cudaStream_t)stream, -1, nullptr, nullptr, 0, &block, mode == HOFEM_SWEEP_FUSED ? line_offset : 0);
+}
+
+hofem_status hofem_residual_slab(hofem_plan_t p, int stage, long long e0, long long e1, const double* a,
+                                 const double* b, const double* f, double* out0, double* out1, int out_fp32, int nrhs,
+                                 void* stream) {
+  if (!p) return fail(HOFEM_ERR_INVALID_ARG, "plan is NULL");
+  const int N = p->N, n0 = p->ax[0].h.n, K0 = p->K[0];
+  const long long M0 = p->M[0];
+  if (stage < 0 || stage > 1 || e0 < 0 || e1 <= e0 || e1 > K0 || nrhs < 1 || !a || !out0 ||
+      (stage == 0 && !out1) || (stage == 1 && !b))
+    return fail(HOFEM_ERR_INVALID_ARG, "bad stage, element range, nrhs or pointers");
+  cudaStream_t s = (cudaStream_t)stream;
+  hofem_status st = reserve(p, 1);   // scratch of the 3D first pass
+  if (st != HOFEM_OK) return st;
+  const long long rows = std::min<long long>(e1 * n0, M0) - e0 * n0;
+  const long long pre = e0 > 0 ? 1 : 0, post = e1 < K0 ? n0 : 0, ext = pre + rows + post;
+  long long plane = 1;
+  for (int i = 1; i < N; ++i) plane *= p->M[i];
+  double sc[3];
+  for (int i = 0; i < N; ++i) sc[i] = 4.0 * (double)p->K[i] * (double)p->K[i] / (p->X[i] * p->X[i]);
+  const bool uni = uniform_stiffness(p, sc);
+  const double cCP = uni ? p->alpha / (sc[0] * p->ax[0].h.a_scale) : p->alpha;
+  if (stage == 0) {
+    // the sweeps along x_N .. x_2 of the slab's rows, into the owned rows of the extended arrays
+    for (int q = 0; q < nrhs; ++q) {
+      const double* uq = a + (size_t)q * rows * plane;
+      double* t0 = out0 + ((size_t)q * ext + pre) * plane;
+      double* t1 = out1 + ((size_t)q * ext + pre) * plane;
+      if (N == 2) {
+        ApplyBlock blk;
+        blk.g = Geo{rows, 1};
+        if ((st = run_apply(p, 1, uq, nullptr, t0, t1, nullptr, sc[1], cCP, 1, s, uni, false, &blk)) != HOFEM_OK)
+          return st;
+      } else {
+        double** t = p->tmp64;
+        ApplyBlock b2, b1;
+        b2.g = Geo{rows * p->M[1], 1};
+        b1.g = Geo{rows, p->M[2]};
+        if ((st = run_apply(p, 2, uq, nullptr, t[0], t[1], nullptr, sc[2], cCP, 1, s, uni, false, &b2)) != HOFEM_OK)
+          return st;
+        if ((st = run_apply(p, 1, t[0], t[1], t0, t1, nullptr, sc[1], 0.0, 1, s, uni, false, &b1)) != HOFEM_OK)
+          return st;
+      }
+    }
+    return HOFEM_OK;
+  }
+  // the sweep along x_1 over the slab's elements, its halo rows read from the extended arrays
+  ApplyBlock blk;
+  blk.g = Geo{1, plane};
+  blk.q0 = e0 * n0 - pre;
+  blk.in_rows = ext;
+  blk.e0 = e0;
+  blk.elems = e1 - e0;
+  blk.out0 = e0 * n0;
+  blk.out_rows = rows;
+  return run_apply(p, 0, a, b, nullptr, out0, f, sc[0], 0.0, nrhs, s, uni, out_fp32 != 0, &blk);
+}
+
+hofem_status hofem_axpy(double* y, double c, const double* x, long long count, void* stream) {
+  if (count < 0 || (count > 0 && (!y || !x))) return fail(HOFEM_ERR_INVALID_ARG, "bad pointers or count");
+  if (count == 0) return HOFEM_OK;
+  HOFEM_CUDA(launch_axpy(y, c, x, count, (cudaStream_t)stream), "axpy launch");
+  return HOFEM_OK;
 }
 
 hofem_status hofem_copy_block(const double* src, double* dst, long long batch, long long rows, long long cols,

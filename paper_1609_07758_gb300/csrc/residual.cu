@@ -183,9 +183,16 @@ __global__ void __launch_bounds__(kApplyThreads, N <= kApplyMinb3MaxN ? 3 : N <=
   const long long l0 = tix * W;
   const long long nl = contiguous ? P.outer_per_rhs : P.inner;
   const int wvalid = (int)min((long long)W, nl - l0);
-  const long long p0 = (long long)seg * E * n - 1;   // dof of tile row 0
+  const long long p0 = (P.blk_e0 + seg * E) * n - 1;   // global dof of tile row 0
+  // element offsets of dof p in the input and the output lines
+  const long long Li = P.blk_in_rows, Lo = P.blk_out_rows;
+  auto gin = [&](long long p, int w) -> size_t {
+    const long long i = p - P.blk_q0;
+    return contiguous ? (size_t)(o * P.outer_per_rhs + l0 + w) * Li + i : ((size_t)o * Li + i) * P.inner + l0 + w;
+  };
   auto gidx = [&](long long p, int w) -> size_t {
-    return contiguous ? (size_t)(o * P.outer_per_rhs + l0 + w) * M + p : ((size_t)o * M + p) * P.inner + l0 + w;
+    const long long i = p - P.blk_out0;
+    return contiguous ? (size_t)(o * P.outer_per_rhs + l0 + w) * Lo + i : ((size_t)o * Lo + i) * P.inner + l0 + w;
   };
   for (int it = threadIdx.x; it < R * W; it += blockDim.x) {
     int r, w;
@@ -198,8 +205,8 @@ __global__ void __launch_bounds__(kApplyThreads, N <= kApplyMinb3MaxN ? 3 : N <=
     }
     const long long p = p0 + r;
     double vp = 0.0, vq = 0.0;
-    if (w < wvalid && p >= 0 && p < M) {
-      const size_t g = gidx(p, w);
+    if (w < wvalid && p >= 0 && p < M && p >= P.blk_q0 && p < P.blk_q0 + Li) {
+      const size_t g = gin(p, w);
       vp = __ldg(P.P + g);
       if (QC) vq = __ldg(P.Q + g);
     }
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(kApplyThreads, N <= kApplyMinb3MaxN ? 3 : N <=
         w = it - (r - 1) * W;
       }
       const long long p = p0 + r;
-      ok[u] = it < total && w < wvalid && p < M;
+      ok[u] = it < total && w < wvalid && p < M && p >= P.blk_out0 && p < P.blk_out0 + Lo;
       rr[u] = r;
       ww[u] = w;
       gg[u] = ok[u] ? gidx(p, w) : 0;

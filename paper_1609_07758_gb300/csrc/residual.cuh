@@ -33,6 +33,11 @@ struct ApplyParams {
                                            // out2 unscaled, cA applied by the last sweep
   int out2_f32;                            // kApplyLast: out2 is an FP32 array (the right-hand
                                            // side of an FP32 correction solve)
+  // Lines that hold only part of the grid along the sweep's axis (a slab of x_1 rows of a
+  // problem split over GPUs).  Input line l holds global dofs q0 .. q0 + in_rows - 1, output
+  // lines (out1, out2, f) dofs out0 .. out0 + out_rows - 1; segment 0 starts at element e0.
+  // The whole-grid sweep: q0 = out0 = e0 = 0, in_rows = out_rows = M.
+  long long blk_q0, blk_in_rows, blk_e0, blk_out0, blk_out_rows;
   const double* P;
   const double* Q;                         // kApplyMid, kApplyLast
   double* out1;                            // kApplyFirst, kApplyMid

@@ -18,8 +18,12 @@ geometry and calls the exchange.  ``SlabSolver.solve`` drives one rank with a co
 (``TorchComm``: ``torch.distributed.all_to_all_single``, NCCL on GPUs); the three phases
 are also public, so that one process can drive several slabs phase by phase.
 
-Scope: plans in FP64 (and unrefined FP32); refinement with a distributed residual is not
-part of this module.
+Refined solves (``SlabSolver.solve_refined``) add the FP64 residual of each slab
+(``hofem_residual_slab``): the operator's sweeps along x_N .. x_2 are local; the sweep along
+x_1 needs the previous slab's last row and the next slab's first n rows of its two
+intermediate arrays, which one more (small) all-to-all exchanges; slabs then hold whole
+elements along x_1 (``SlabLayout.by_elements``).  The correction solves run the plan's
+low-precision sweeps through the same two-exchange path, and ``hofem_axpy`` adds them to u.
 """
 from dataclasses import dataclass
 
@@ -52,6 +56,30 @@ class SlabLayout:
         self.cols = split(self.M[1], self.parts)
         self.tail = 1 if len(self.M) == 2 else self.M[2]     # elements per x_2 index
 
+    @classmethod
+    def by_elements(cls, M, K0, n0, parts):
+        """Slabs of whole elements along x_1 (needed by the slab residual): slab r owns elements
+        e_r .. e_{r+1} - 1, i.e. the dof rows e_r n0 .. min(e_{r+1} n0, M_1) - 1."""
+        L = cls(tuple(M), parts)
+        if parts > K0:
+            raise ValueError("parts must not exceed the elements along x_1")
+        L.elems = [(s, s + c) for s, c in split(K0, parts)]
+        L.rows = [(e0 * n0, min(e1 * n0, M[0]) - e0 * n0) for e0, e1 in L.elems]
+        if min(c for _, c in L.rows) < 1:
+            raise ValueError("every slab needs at least one row")
+        L.K0, L.n0 = K0, n0
+        return L
+
+    def lead_rows(self, rank):
+        """The rows a slab sends to the previous one: its first n0, or all it has (the last
+        element's right node is the Dirichlet boundary)."""
+        return min(self.n0, self.rows[rank][1])
+
+    def halo(self, rank):
+        """(rows before, rows after) of a slab's halo for the operator along x_1."""
+        e0, e1 = self.elems[rank]
+        return (1 if e0 > 0 else 0), (self.n0 if e1 < self.K0 else 0)
+
     def slab_shape(self, rank, nrhs):
         return (nrhs, self.rows[rank][1]) + tuple(self.M[1:])
 
@@ -78,6 +106,12 @@ class GpuOps:
     def copy_block(self, src, src_off, dst, dst_off, batch, rows, cols, src_ld, dst_ld, src_bs, dst_bs):
         binding.hofem_copy_block(src.data_ptr() + 8 * src_off, dst.data_ptr() + 8 * dst_off, batch, rows, cols,
                                  src_ld, dst_ld, src_bs, dst_bs, self.stream)
+
+    def residual_slab(self, stage, e0, e1, a, b, f, out0, out1, nrhs):
+        binding.hofem_residual_slab(self.plan.handle, stage, e0, e1, a, b, f, out0, out1, 0, nrhs, self.stream)
+
+    def axpy(self, y, c, x, count):
+        binding.hofem_axpy(y, c, x, count, self.stream)
 
     def empty(self, count, like):
         import torch
@@ -166,3 +200,82 @@ class SlabSolver:
         send = self.fused(recv)
         recv = comm.all_to_all(send, L.recv_counts_1(r, q), L.send_counts_1(r, q), self.ops)
         self.inverse(recv, u)
+
+    # ---- the slab residual r = f - A u (layout from SlabLayout.by_elements)
+    def _ext_rows(self):
+        pre, post = self.L.halo(self.rank)
+        return pre, self.L.rows[self.rank][1], post
+
+    def residual_local(self, u):
+        """Stage 0: the two intermediates, owned rows filled; returns (t0, t1, halo pack)."""
+        L, r, ops, q = self.L, self.rank, self.ops, self.nrhs
+        pre, rows, post = self._ext_rows()
+        plane = L.M[1] * L.tail
+        ext = pre + rows + post
+        t0, t1 = ops.empty(q * ext * plane, u), ops.empty(q * ext * plane, u)
+        e0, e1 = L.elems[r]
+        ops.residual_slab(0, e0, e1, u, None, None, t0, t1, q)
+        # pack by destination: the first rows for rank r - 1, then the last row for rank r + 1
+        up, down = (1 if r + 1 < L.parts else 0), (L.lead_rows(r) if r > 0 else 0)
+        send = ops.empty(2 * q * (up + down) * plane, u)
+        off = 0
+        if down:
+            for t in (t0, t1):
+                ops.copy_block(t, pre * plane, send, off, q, down, plane, plane, plane, ext * plane, down * plane)
+                off += q * down * plane
+        if up:
+            for t in (t0, t1):
+                ops.copy_block(t, (pre + rows - 1) * plane, send, off, q, 1, plane, plane, plane, ext * plane, plane)
+                off += q * plane
+        return t0, t1, send
+
+    def halo_counts(self):
+        """(send, recv) counts of the halo exchange, per rank."""
+        L, r, q = self.L, self.rank, self.nrhs
+        plane = L.M[1] * L.tail
+        send = [0] * L.parts
+        recv = [0] * L.parts
+        if r > 0:
+            send[r - 1] = 2 * q * L.lead_rows(r) * plane     # my first rows: its 'after' halo
+            recv[r - 1] = 2 * q * plane                      # its last row: my 'before' halo
+        if r + 1 < L.parts:
+            send[r + 1] = 2 * q * plane
+            recv[r + 1] = 2 * q * L.lead_rows(r + 1) * plane
+        return send, recv
+
+    def residual_last(self, t0, t1, recv, f, out):
+        """Stage 1: unpack the halo rows, the sweep along x_1: out = f - A u on the slab."""
+        L, r, ops, q = self.L, self.rank, self.ops, self.nrhs
+        pre, rows, post = self._ext_rows()
+        plane = L.M[1] * L.tail
+        ext = pre + rows + post
+        off = 0
+        if r > 0:                                       # from rank r - 1: its last row, both arrays
+            for t in (t0, t1):
+                ops.copy_block(recv, off, t, 0, q, 1, plane, plane, plane, plane, ext * plane)
+                off += q * plane
+        if r + 1 < L.parts:                             # from rank r + 1: its first rows
+            lead = L.lead_rows(r + 1)
+            for t in (t0, t1):
+                ops.copy_block(recv, off, t, (pre + rows) * plane, q, lead, plane, plane, plane, lead * plane,
+                               ext * plane)
+                off += q * lead * plane
+        e0, e1 = L.elems[r]
+        ops.residual_slab(1, e0, e1, t0, t1, f, out, None, q)
+
+    def residual(self, f, u, out, comm):
+        t0, t1, send = self.residual_local(u)
+        sc, rc = self.halo_counts()
+        recv = comm.all_to_all(send, sc, rc, self.ops)
+        self.residual_last(t0, t1, recv, f, out)
+
+    def solve_refined(self, f, u, comm, corrections):
+        """u = A^{-1} f: the plan's low-precision solve, then `corrections` steps of
+        r = f - A u (FP64, slab residual), delta = solve(r), u += delta."""
+        self.solve(f, u, comm)
+        r = self.ops.empty(u.numel(), u)
+        d = self.ops.empty(u.numel(), u)
+        for _ in range(corrections):
+            self.residual(f, u, r, comm)
+            self.solve(r, d, comm)
+            self.ops.axpy(u, 1.0, d, u.numel())

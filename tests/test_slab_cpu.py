@@ -63,6 +63,51 @@ class OracleOps:
     def empty(self, count, like):
         return torch.zeros(count, dtype=torch.float64)
 
+    # hofem_residual_slab with intermediates of this class's own choosing: t0 = u with the mass
+    # matrices of x_2..x_N, t1 = the rest of the operator along x_2..x_N; the sweep along x_1
+    # then adds s_1 A_1 t0 + C_1 t1 over the slab's rows, read from the rows with their halo
+    def set_operator(self, ns, Ks, Xs, alpha):
+        from oracle import assemble
+        self.ns, self.Ks, self.alpha_op = ns, Ks, alpha
+        self.mats = [assemble.global_1d_sparse(n, K) for n, K in zip(ns, Ks)]
+        self.sc = [4.0 * (K / X) ** 2 for K, X in zip(Ks, Xs)]
+
+    def residual_slab(self, stage, e0, e1, a, b, f, out0, out1, nrhs):
+        from oracle.assemble import _mode_product
+        N, n0, K0 = len(self.Ks), self.ns[0], self.Ks[0]
+        M = [m[0].shape[0] for m in self.mats]
+        rows = min(e1 * n0, M[0]) - e0 * n0
+        pre, post = (1 if e0 > 0 else 0), (n0 if e1 < K0 else 0)
+        ext = pre + rows + post
+        plane = int(np.prod(M[1:]))
+        if stage == 0:
+            u = self._view(a, nrhs * rows * plane).reshape([nrhs, rows] + M[1:])
+            t0 = u
+            for m in range(1, N):
+                t0 = _mode_product(t0, self.mats[m][1], m + 1)
+            t1 = self.alpha_op * t0
+            for i in range(1, N):
+                t = u
+                for m in range(1, N):
+                    t = _mode_product(t, self.mats[m][0] if m == i else self.mats[m][1], m + 1)
+                t1 = t1 + self.sc[i] * t
+            for arr, val in ((out0, t0), (out1, t1)):
+                v = self._view(arr, nrhs * ext * plane).reshape(nrhs, ext, plane)
+                v[:, pre:pre + rows] = val.reshape(nrhs, rows, plane)
+            return
+        q0 = e0 * n0 - pre
+        hi = min(q0 + ext, M[0])
+        A0, C0 = (m.tocsr()[e0 * n0:e0 * n0 + rows, q0:hi] for m in self.mats[0])
+        t0 = self._view(a, nrhs * ext * plane).reshape(nrhs, ext, plane)[:, :hi - q0]
+        t1 = self._view(b, nrhs * ext * plane).reshape(nrhs, ext, plane)[:, :hi - q0]
+        r = np.stack([self.sc[0] * (A0 @ t0[q]) + C0 @ t1[q] for q in range(nrhs)])
+        if f is not None:
+            r = self._view(f, nrhs * rows * plane).reshape(nrhs, rows, plane) - r
+        self._view(out0, nrhs * rows * plane)[:] = r.reshape(-1)
+
+    def axpy(self, y, c, x, count):
+        self._view(y, count)[:] += c * self._view(x, count)
+
 
 CASES = {
     "2d": dict(ns=[3, 2], Ks=[8, 6], Xs=[1.0, 1.5], alpha=0.0, nrhs=2),
@@ -89,6 +134,58 @@ def _rank_main(rank, world, port, case, out_dir):
     solver.solve(f_local, u_local, slab.TorchComm())
     np.save(os.path.join(out_dir, f"{case}_u{rank}.npy"), u_local.numpy())
     dist.destroy_process_group()
+
+
+def _residual_rank(rank, world, port, case, out_dir):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    from oracle import spectrum
+    from paper_1609_07758_gb300 import slab
+    c = CASES[case]
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    specs = [spectrum.spectrum(n, K, X) for n, K, X in zip(c["ns"], c["Ks"], c["Xs"])]
+    M = tuple(s.M for s in specs)
+    layout = slab.SlabLayout.by_elements(M, c["Ks"][0], c["ns"][0], world)
+    ops = OracleOps(specs, c["alpha"])
+    ops.set_operator(c["ns"], c["Ks"], c["Xs"], c["alpha"])
+    rng = np.random.default_rng(9)
+    f = rng.standard_normal((c["nrhs"],) + M)
+    u = rng.standard_normal((c["nrhs"],) + M)
+    start, rows = layout.rows[rank]
+    fl = torch.from_numpy(np.ascontiguousarray(f[:, start:start + rows]))
+    ul = torch.from_numpy(np.ascontiguousarray(u[:, start:start + rows]))
+    solver = slab.SlabSolver(layout, rank, ops, c["nrhs"])
+    r = torch.zeros_like(fl)
+    solver.residual(fl, ul, r, slab.TorchComm())        # r = f - A u on the slab
+    v = torch.zeros_like(fl)
+    solver.solve_refined(fl, v, slab.TorchComm(), 2)    # refined solve (exact inner solves here)
+    np.save(os.path.join(out_dir, f"{case}_r{rank}.npy"), r.numpy())
+    np.save(os.path.join(out_dir, f"{case}_v{rank}.npy"), v.numpy())
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("case,world", [("2d", 2), ("2d", 3), ("3d", 3)])
+def test_slab_residual_and_refined_solve_over_gloo_ranks_match_the_oracle(tmp_path, case, world):
+    """The slab residual's halo exchange (the previous slab's last row, the next slab's first n
+    rows of both intermediates) against the oracle's operator on the whole grid, and the refined
+    slab solve against the oracle's solve."""
+    import torch.multiprocessing as mp
+    from oracle import assemble, solve as osolve
+    port = _free_port()
+    mp.start_processes(_residual_rank, args=(world, port, case, str(tmp_path)), nprocs=world,
+                       start_method="spawn", join=True)
+    c = CASES[case]
+    M = tuple(n * K - 1 for n, K in zip(c["ns"], c["Ks"]))
+    rng = np.random.default_rng(9)
+    f = rng.standard_normal((c["nrhs"],) + M)
+    u = rng.standard_normal((c["nrhs"],) + M)
+    r = np.concatenate([np.load(tmp_path / f"{case}_r{k}.npy") for k in range(world)], axis=1)
+    ref = f - assemble.apply_operator(u, c["ns"], c["Ks"], c["Xs"], c["alpha"])
+    assert np.linalg.norm(r - ref) <= 1e-13 * np.linalg.norm(ref)
+    v = np.concatenate([np.load(tmp_path / f"{case}_v{k}.npy") for k in range(world)], axis=1)
+    vref = osolve.solve_tensor(f, c["ns"], c["Ks"], c["Xs"], c["alpha"])
+    assert np.linalg.norm(v - vref) <= 1e-12 * np.linalg.norm(vref)
 
 
 @pytest.mark.parametrize("case,world", [("2d", 2), ("2d", 3), ("3d", 2), ("3d", 3)])
