@@ -52,6 +52,8 @@ def parse_args():
                     help="skip the 3D workloads (n=4 K=128; n=8 K=64 with 16 RHS), refined vs FP64")
     ap.add_argument("--batch-tune", action="store_true",
                     help="autotune every problem of the batch first (84 s for 512 problems; 3%% faster solves)")
+    ap.add_argument("--no-slab", action="store_true",
+                    help="under torchrun: skip the one problem split over all ranks (strong scaling)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the widened paths at the same size (on-device f^h, algorithm (b), a heat "
                          "step, the variable-coefficient operator and PCG)")
@@ -216,6 +218,36 @@ def reference_arm(args, rank, world):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def slab_strong(hofem, torch, stream, rank, world, steps=3, corrections=2):
+    """One config-2 problem split over all ranks by slabs of x_1 (paper_1609_07758_gb300.slab):
+    the refined solve with two all-to-alls per inner solve and a halo exchange per residual,
+    timed like the headline (CUDA events, barrier, max over ranks); unknowns / time."""
+    from paper_1609_07758_gb300 import inputs, slab
+    M = N_ORDER * K_ELEM - 1
+    L = slab.SlabLayout.by_elements((M, M), K_ELEM, N_ORDER, world)
+    plan = hofem.Plan(2, [K_ELEM, K_ELEM], N_ORDER, [X_LEN, X_LEN], hofem.HOFEM_FP32_REFINED)
+    solver = slab.SlabSolver(L, rank, slab.GpuOps(plan, stream), 1)
+    start, rows = L.rows[rank]
+    f = torch.from_numpy(inputs.smooth_sine_rhs(2, N_ORDER, K_ELEM)[:, start:start + rows].copy()).cuda()
+    u = torch.empty_like(f)
+    comm = slab.TorchComm()
+    solver.solve_refined(f, u, comm, corrections)                    # warm-up
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        solver.solve_refined(f, u, comm, corrections)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
+    plan.close()
+    return {"workload": WORKLOAD, "ranks": world, "corrections": corrections, "ms_per_solve": ms,
+            "unknowns_per_s": UNKNOWNS / (ms / 1e3), "scaling": "strong",
+            "path": "slabs of x_1 rows; 2 all-to-alls per inner solve, 1 halo exchange per residual"}
 
 
 def batch_paths(hofem, torch, stream, tune, steps=3, rank=0, world=1):
@@ -526,6 +558,7 @@ def main():
         extras = extra_paths(hofem, torch, f, u, stream, args)
     batched = None if args.no_batch else batch_paths(hofem, torch, stream, args.batch_tune, rank=rank, world=world)
     configs = None if (args.no_configs or world > 1) else config_paths(hofem, torch, stream)
+    strong = None if (args.no_slab or world == 1) else slab_strong(hofem, torch, stream, rank, world)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -620,6 +653,7 @@ def main():
         **({"extras_ms": extras} if extras else {}),
         **({"batched": batched} if batched else {}),
         **({"configs": configs} if configs else {}),
+        **({"slab_one_problem": strong} if strong else {}),
         "clocks": clock_info,
     }
     if rank == 0:
