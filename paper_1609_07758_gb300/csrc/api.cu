@@ -549,6 +549,16 @@ hofem_status solve_once(hofem_plan_s* p, const double* f, double* u, int nrhs, b
 
 // One operator sweep along `axis` (modes in residual.cuh): Q == nullptr is the first
 // sweep (out1 required), Q and out1 a middle one, Q without out1 the last one.
+// Elements per CTA of an operator sweep without a tuned value: the largest of 16 / 8 / 4
+// whose tile lets three CTAs share an SM (orders compiled for it), else 16, halved later to
+// fit shared memory (measured best at n = 9, K = 1024: E = 8 at three CTAs per SM).
+int apply_default_elems(int n) {
+  int E = 16;
+  if (n <= kApplyMinb3MaxN)
+    while (E > 4 && apply_smem_bytes(n, E) > kApplySmem3) E /= 2;
+  return E;
+}
+
 // Lines of an operator sweep that are not the plan's grid: the block's geometry (one right-
 // hand side's outer lines and inner stride) and, when elems > 0, a stretch of the sweep's
 // axis -- input rows from global dof q0 (in_rows of them), output rows from dof out0
@@ -567,12 +577,7 @@ hofem_status run_apply(hofem_plan_s* p, int axis, const double* P_, const double
   const bool strided = g.inner > 1;
   ApplyParams P{};
   const int W = kApplyLines;
-  // elements per CTA: the largest of 16 / 8 / 4 whose tile lets three CTAs share an SM
-  // (orders compiled for it), else 16 halved below to fit (measured best at n = 9, K = 1024:
-  // E = 8 at three CTAs per SM)
-  int E = 16;
-  if (A.h.n <= kApplyMinb3MaxN)
-    while (E > 4 && apply_smem_bytes(A.h.n, E) > kApplySmem3) E /= 2;
+  int E = apply_default_elems(A.h.n);
   {
     int tE = 0, unused = 0;
     const TuneKey key = apply_key(p, axis, Q_ == nullptr ? kApplyFirst : (out1 ? kApplyMid : kApplyLast), nrhs);
@@ -943,24 +948,34 @@ hofem_status tune_plan(hofem_plan_s* p, int nrhs, cudaStream_t s, int* measured)
     aps.push_back({1, t[0], t[1], t[2], t[3], 0.0});
     aps.push_back({0, t[2], t[3], nullptr, p->r64, 0.0});
   }
+  // the kernel form the solves run (uniform scale or not)
+  double sc[3];
+  for (int i = 0; i < N; ++i) sc[i] = 4.0 * (double)p->K[i] * (double)p->K[i] / (p->X[i] * p->X[i]);
+  const bool uni = uniform_stiffness(p, sc);
   for (const Ap& ap : aps) {
     const int mode = ap.Q == nullptr ? kApplyFirst : (ap.o1 ? kApplyMid : kApplyLast);
     const TuneKey key = apply_key(p, ap.axis, mode, nrhs);
     int a0, b0;
     if (tuned_lookup(key, &a0, &b0)) continue;
-    double best = 1e30;
+    const int dE = std::min(apply_default_elems(p->ax[ap.axis].h.n), p->ax[ap.axis].h.K);
+    double best = 1e30, t_default = 1e30;
     int bE = 0;
     for (int E : {4, 8, 16, 32}) {
       if (E > p->ax[ap.axis].h.K || apply_smem_bytes(p->ax[ap.axis].h.n, E) > kSmemLimit) continue;
       g_force_a = E;
       bool ok = false;
       const double ms = time_launches(s, [&]() {
-        return run_apply(p, ap.axis, ap.P, ap.Q, ap.o1, ap.o2, nullptr, 1.0, ap.cCP, nrhs, s);
+        return run_apply(p, ap.axis, ap.P, ap.Q, ap.o1, ap.o2, nullptr, 1.0, ap.cCP, nrhs, s, uni);
       }, &ok);
       g_force_a = 0;
       ++*measured;
       if (ok && ms < best) { best = ms; bE = E; }
+      if (ok && E == dE) t_default = ms;
     }
+    // the built-in shape unless a candidate is clearly faster: near-equal timings of one
+    // sweep in isolation do not rank the shapes for a solve whose copies and neighbouring
+    // kernels share the GPU (three CTAs per SM hide more of them)
+    if (t_default < 1e30 && best > 0.97 * t_default) bE = dE;
     if (bE > 0) {
       std::lock_guard<std::mutex> lock(g_tune_mu);
       g_tuned[key] = {bE, 0};
