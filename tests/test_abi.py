@@ -81,6 +81,22 @@ def test_null_plan_calls_fail_cleanly(lib):
     lib.hofem_destroy(None)
 
 
+def test_slab_entry_points_check_arguments_on_the_host(lib):
+    """The block sweep, block copy, slab residual and axpy entry points refuse bad arguments
+    before touching a device (NULL plans, negative or inconsistent sizes, missing arrays)."""
+    import paper_1609_07758_gb300  # noqa: F401  (argtypes)
+    from paper_1609_07758_gb300 import binding
+    binding.load_library()
+    assert lib.hofem_sweep(None, 0, 0, None, None, 1, 1, 0, None) == 1
+    assert lib.hofem_residual_slab(None, 0, 0, 1, None, None, None, None, None, 0, 1, None) == 1
+    assert lib.hofem_copy_block(None, None, -1, 1, 1, 1, 1, 1, 1, None) == 1
+    assert lib.hofem_copy_block(None, None, 1, 2, 4, 4, 4, 8, 8, None) == 1      # NULL arrays
+    assert lib.hofem_copy_block(None, None, 1, 0, 4, 4, 4, 0, 0, None) == 0      # nothing to copy
+    assert lib.hofem_axpy(None, 1.0, None, -1, None) == 1
+    assert lib.hofem_axpy(None, 1.0, None, 0, None) == 0
+    assert lib.hofem_axpy(None, 1.0, None, 5, None) == 1
+
+
 def test_batch_and_tuner_host_checks(lib):
     out = ctypes.c_void_p()
     lib.hofem_batch_plan.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
