@@ -181,7 +181,7 @@ template <class C> __device__ __forceinline__ float fseq(const float* tile, int 
   const float* t = tile + w * C::MS;
   const float v1 = t[c == 0 ? j * C::N - 1 : j * C::N + c - 1];
   const float v2 = t[(j - 1) * C::N + C::N - c - 1];
-  return c == 0 ? v1 : v1 + v2;
+  return fmaf(c == 0 ? 0.f : 1.f, v2, v1);   // the weight is uniform per job: no select per value
 }
 
 // twt: the pass's inter-stage twiddles, twt[k2 L + r] = w_K^{r k2} (X) or w_2K^{r (2 k2 + 1)}
@@ -250,8 +250,11 @@ template <class C> __device__ __forceinline__ void extract_z(const float2 (&v)[3
 // clamped, valid indices and masked afterwards (no branch around a load).
 template <class C, bool FWD>
 __device__ __forceinline__ float2 job_input(const float* tile, const RJob& jb, bool active, int j) {
+  // masks only where the shape needs them (known at compile time): idle lane groups in the
+  // last job round, node jobs without a second line; x_0 = 0 is set by the caller
+  constexpr bool MASK_ACTIVE = (C::NJOBS % (C::NW * C::G)) != 0;
+  constexpr bool MASK_B = (C::N % 2 == 1) && (C::W % 2 == 1);
   const int jj = j > 0 ? j : 1;
-  const bool ok = active && j > 0, okb = ok && jb.cb >= 0;
   const int cb = jb.cb >= 0 ? jb.cb : jb.ca;
   float a, b;
   if (FWD) {
@@ -261,7 +264,12 @@ __device__ __forceinline__ float2 job_input(const float* tile, const RJob& jb, b
     a = tile[jb.wa * C::MS + (jj - 1) * C::N + slotc<C>(jb.ca)];
     b = tile[jb.wb * C::MS + (jj - 1) * C::N + slotc<C>(cb)];
   }
-  return make_float2(ok ? a : 0.f, okb ? b : 0.f);
+  if (MASK_ACTIVE) {
+    a = active ? a : 0.f;
+    b = active ? b : 0.f;
+  }
+  if (MASK_B) b = jb.cb >= 0 ? b : 0.f;
+  return make_float2(a, b);
 }
 
 // All DST jobs of the tile.  FWD: pre-combined physical sequences -> 2 x DST in the
@@ -286,11 +294,13 @@ __device__ __forceinline__ void dst_jobs(float* tile, float* scr, const float2* 
     float2 v[32], d[16];
 #pragma unroll
     for (int n2 = 0; n2 < 32; ++n2) v[n2] = job_input<C, FWD>(tile, jb, active, r + L * n2);
+    if (r == 0) v[0] = make_float2(0.f, 0.f);   // x_0 = 0 (j = r + L n2 is 0 only here)
     __syncwarp();    // the previous round's reads of the transpose area are done
     group_fft<C, false>(v, win, lane, g, r, twx);
     extract_x<C>(v, d, g, r);
 #pragma unroll
     for (int n2 = 0; n2 < 32; ++n2) v[n2] = rot64(job_input<C, FWD>(tile, jb, active, r + L * n2), n2);
+    if (r == 0) v[0] = make_float2(0.f, 0.f);
     __syncthreads();   // every job of this round has read its inputs
     float* ta = tile + jb.wa * C::MS + slotc<C>(jb.ca);
     float* tb = jb.cb >= 0 ? tile + jb.wb * C::MS + slotc<C>(jb.cb) : nullptr;
