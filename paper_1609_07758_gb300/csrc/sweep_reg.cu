@@ -174,16 +174,6 @@ template <class C> __device__ __forceinline__ RJob rjob(int jx) {
 
 template <class C> __device__ __forceinline__ int slotc(int c) { return c == 0 ? C::N - 1 : c - 1; }
 
-// forward pre-combined sequence of component c of line w at j (1..K-1); both reads are
-// unconditional (for the nodes, c = 0, the second index is the first one), so that the
-// unrolled loads of a job issue back to back
-template <class C> __device__ __forceinline__ float fseq(const float* tile, int w, int c, int j) {
-  const float* t = tile + w * C::MS;
-  const float v1 = t[c == 0 ? j * C::N - 1 : j * C::N + c - 1];
-  const float v2 = t[(j - 1) * C::N + C::N - c - 1];
-  return fmaf(c == 0 ? 0.f : 1.f, v2, v1);   // the weight is uniform per job: no select per value
-}
-
 // twt: the pass's inter-stage twiddles, twt[k2 L + r] = w_K^{r k2} (X) or w_2K^{r (2 k2 + 1)}
 // (Z), a K-entry table in global memory (L1-resident) laid out so that the lanes of a group
 // read consecutive entries.
@@ -245,24 +235,44 @@ template <class C> __device__ __forceinline__ void extract_z(const float2 (&v)[3
   }
 }
 
-// Input x_j (j = r + L n2) of a job: the pre-combined physical sequences (FWD) or the
-// spectral ones (inverse); zero at j = 0 and for groups without a job.  Reads are made at
-// clamped, valid indices and masked afterwards (no branch around a load).
-template <class C, bool FWD>
-__device__ __forceinline__ float2 job_input(const float* tile, const RJob& jb, bool active, int j) {
+// Where job jb reads its inputs: x_j = t[o1 + j N] + wt t[o2 + j N] for each of its two
+// sequences (j = 1..K-1).  Forward: the pre-combined physical sequence of component c,
+// t[j N + c - 1] + t[j N - c - 1] (the nodes, c = 0: t[j N - 1], weight 0); inverse: the
+// spectral slot (weight 0).  Both reads are unconditional, so that the unrolled loads of
+// a job issue back to back, and the weight is uniform per job (no select per value).
+struct JobIn {
+  int a1, a2, b1, b2;
+  float wa, wb;
+};
+template <class C> __device__ __forceinline__ JobIn job_in(const RJob& jb, bool fwd) {
+  constexpr int N = C::N, MS = C::MS;
+  const int cb = jb.cb >= 0 ? jb.cb : jb.ca;
+  auto o1 = [&](int c) { return c == 0 ? -1 : (fwd ? c - 1 : c - 1 - N); };
+  auto o2 = [&](int c) { return fwd ? -c - 1 : o1(c); };
+  JobIn ji;
+  ji.a1 = jb.wa * MS + o1(jb.ca);
+  ji.a2 = jb.wa * MS + o2(jb.ca);
+  ji.b1 = jb.wb * MS + o1(cb);
+  ji.b2 = jb.wb * MS + o2(cb);
+  ji.wa = fwd && jb.ca != 0 ? 1.f : 0.f;
+  ji.wb = fwd && cb != 0 ? 1.f : 0.f;
+  return ji;
+}
+
+// Input x_j (j = r + L n2) of a job; zero at j = 0 and for groups without a job.  Reads
+// are made at clamped, valid indices and masked afterwards (no branch around a load).
+// FWDM: 0 inverse, 1 forward (known at compile time), 2 either (both reads made).
+template <class C, int FWDM>
+__device__ __forceinline__ float2 job_input(const float* tile, const RJob& jb, const JobIn& ji, bool active, int j) {
   // masks only where the shape needs them (known at compile time): idle lane groups in the
   // last job round, node jobs without a second line; x_0 = 0 is set by the caller
   constexpr bool MASK_ACTIVE = (C::NJOBS % (C::NW * C::G)) != 0;
   constexpr bool MASK_B = (C::N % 2 == 1) && (C::W % 2 == 1);
-  const int jj = j > 0 ? j : 1;
-  const int cb = jb.cb >= 0 ? jb.cb : jb.ca;
-  float a, b;
-  if (FWD) {
-    a = fseq<C>(tile, jb.wa, jb.ca, jj);
-    b = fseq<C>(tile, jb.wb, cb, jj);
-  } else {
-    a = tile[jb.wa * C::MS + (jj - 1) * C::N + slotc<C>(jb.ca)];
-    b = tile[jb.wb * C::MS + (jj - 1) * C::N + slotc<C>(cb)];
+  const int o = (j > 0 ? j : 1) * C::N;
+  float a = tile[ji.a1 + o], b = tile[ji.b1 + o];
+  if (FWDM != 0) {
+    a = fmaf(ji.wa, tile[ji.a2 + o], a);
+    b = fmaf(ji.wb, tile[ji.b2 + o], b);
   }
   if (MASK_ACTIVE) {
     a = active ? a : 0.f;
@@ -272,15 +282,16 @@ __device__ __forceinline__ float2 job_input(const float* tile, const RJob& jb, b
   return make_float2(a, b);
 }
 
-// All DST jobs of the tile.  FWD: pre-combined physical sequences -> 2 x DST in the
-// spectral slots.  Inverse: spectral sequences -> 2 x DST (D_j) in the same slots.
+// All DST jobs of the tile.  Forward (FWDM = 1, or 2 with fwd set): pre-combined physical
+// sequences -> 2 x DST in the spectral slots.  Inverse (FWDM = 0, or 2 with fwd clear):
+// spectral sequences -> 2 x DST (D_j) in the same slots.
 // Per job: X from the loaded inputs, its outputs held in registers; the inputs loaded
 // again, times w_64^{n2}, for Z; a barrier (every job's reads of the tile are done); the
 // X outputs stored; Z, whose outputs are stored as they are extracted.  The transposes
 // use the warp's own area of `scr`.
-template <class C, bool FWD>
+template <class C, int FWDM>
 __device__ __forceinline__ void dst_jobs(float* tile, float* scr, const float2* __restrict__ twx,
-                                         const float2* __restrict__ twz) {
+                                         const float2* __restrict__ twz, bool fwd = FWDM == 1) {
   constexpr int L = C::L, N = C::N;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int g = lane / L, r = lane % L;
@@ -291,15 +302,16 @@ __device__ __forceinline__ void dst_jobs(float* tile, float* scr, const float2* 
     const int jx = (round * C::NW + wid) * C::G + g;
     const bool active = jx < C::NJOBS;
     const RJob jb = rjob<C>(active ? jx : 0);
+    const JobIn ji = job_in<C>(jb, FWDM == 2 ? fwd : FWDM == 1);
     float2 v[32], d[16];
 #pragma unroll
-    for (int n2 = 0; n2 < 32; ++n2) v[n2] = job_input<C, FWD>(tile, jb, active, r + L * n2);
+    for (int n2 = 0; n2 < 32; ++n2) v[n2] = job_input<C, FWDM>(tile, jb, ji, active, r + L * n2);
     if (r == 0) v[0] = make_float2(0.f, 0.f);   // x_0 = 0 (j = r + L n2 is 0 only here)
     __syncwarp();    // the previous round's reads of the transpose area are done
     group_fft<C, false>(v, win, lane, g, r, twx);
     extract_x<C>(v, d, g, r);
 #pragma unroll
-    for (int n2 = 0; n2 < 32; ++n2) v[n2] = rot64(job_input<C, FWD>(tile, jb, active, r + L * n2), n2);
+    for (int n2 = 0; n2 < 32; ++n2) v[n2] = rot64(job_input<C, FWDM>(tile, jb, ji, active, r + L * n2), n2);
     if (r == 0) v[0] = make_float2(0.f, 0.f);
     __syncthreads();   // every job of this round has read its inputs
     float* ta = tile + jb.wa * C::MS + slotc<C>(jb.ca);
@@ -669,10 +681,22 @@ __device__ __forceinline__ void work_tile(const SweepParams& P, const TileGeo& g
         if (lane == 0) save[w * (N - 1) + i - 1] = acc;
       }
     }
-    dst_jobs<C, true>(tile, scr, twx, twz);
   }
-  mixing<C, MODE>(tile, save, lrest, P);
-  if constexpr ((MODE & kInv) != 0) dst_jobs<C, false>(tile, scr, twx, twz);
+  if constexpr (MODE == kFwdScaleInv && C::LOGK >= 10) {
+    // one copy of the DST code for both transforms: at K = 1024 two copies of the fused
+    // sweep's code stall its warps on instruction fetch (measured 1.24 -> 1.15 ms at n = 9,
+    // against the inverse's extra read per input); at smaller K the copies are shorter and
+    // the extra reads cost more than they save (n = 4, K = 128: 1.14 -> 1.24 ms)
+#pragma unroll 1
+    for (int ph = 0; ph < 2; ++ph) {
+      if (ph == 1) mixing<C, MODE>(tile, save, lrest, P);
+      dst_jobs<C, 2>(tile, scr, twx, twz, ph == 0);
+    }
+  } else {
+    if constexpr ((MODE & kFwd) != 0) dst_jobs<C, 1>(tile, scr, twx, twz);
+    mixing<C, MODE>(tile, save, lrest, P);
+    if constexpr ((MODE & kInv) != 0) dst_jobs<C, 0>(tile, scr, twx, twz);
+  }
 
   // ---- store: spectral tile (direct sweep) or the post-combine of the inverse transform,
   //   v_j = D_j (nodes),  v_{j-1/2,c} = D_{j-1,c} + D_{j,N-c} + (-1)^{j-1} g_{c or N-c}
