@@ -558,7 +558,12 @@ def main():
         extras = extra_paths(hofem, torch, f, u, stream, args)
     batched = None if args.no_batch else batch_paths(hofem, torch, stream, args.batch_tune, rank=rank, world=world)
     configs = None if (args.no_configs or world > 1) else config_paths(hofem, torch, stream)
-    strong = None if (args.no_slab or world == 1) else slab_strong(hofem, torch, stream, rank, world)
+    strong = None
+    if not (args.no_slab or world == 1):
+        try:
+            strong = slab_strong(hofem, torch, stream, rank, world)
+        except Exception as e:   # a secondary measurement: report it, keep the headline line
+            strong = {"error": f"{type(e).__name__}: {e}"[:300]}
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
