@@ -122,38 +122,36 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 
-template <int R> __host__ __device__ constexpr int brev(int i) {
-  int o = 0;
-  for (int b = 1; b < R; b <<= 1) {
-    o = (o << 1) | (i & 1);
-    i >>= 1;
-  }
-  return o;
-}
-
-// In-register forward DFT of R = 1..32 points, natural order in and out (radix-2
-// decimation in time after a compile-time bit-reversal of the inputs).
+// In-register forward DFT of R = 1..32 points (a power of two), natural order in and out:
+// split radix (decimation in time), X_k = E_k + w^k O1_k + w^3k O3_k from the R/2-point DFT
+// of the even inputs and the R/4-point DFTs of inputs 4m + 1 and 4m + 3, with compile-time
+// twiddles (26 general twiddle products at R = 32 against 34 for radix 2).
 template <int R> __device__ __forceinline__ void dft(float2 (&v)[R]) {
+  if constexpr (R == 2) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if constexpr (R >= 4) {
+    constexpr int H = R / 2, Q = R / 4;
+    float2 e[H], o1[Q], o3[Q];
 #pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int j = brev<R>(i);
-    if (j > i) {
-      const float2 t = v[i];
-      v[i] = v[j];
-      v[j] = t;
+    for (int m = 0; m < H; ++m) e[m] = v[2 * m];
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+      o1[m] = v[4 * m + 1];
+      o3[m] = v[4 * m + 3];
     }
-  }
+    dft<H>(e);
+    dft<Q>(o1);
+    dft<Q>(o3);
 #pragma unroll
-  for (int half = 1; half < R; half <<= 1) {
-#pragma unroll
-    for (int s = 0; s < R; s += 2 * half) {
-#pragma unroll
-      for (int k = 0; k < half; ++k) {
-        const float2 a = v[s + k];
-        const float2 b = rot64(v[s + k + half], k * (32 / half));
-        v[s + k] = cadd(a, b);
-        v[s + k + half] = csub(a, b);
-      }
+    for (int k = 0; k < Q; ++k) {
+      const float2 z1 = rot64(o1[k], k * (64 / R)), z3 = rot64(o3[k], 3 * k * (64 / R));
+      const float2 s = cadd(z1, z3), d = csub(z1, z3);
+      v[k] = cadd(e[k], s);
+      v[k + H] = csub(e[k], s);
+      v[k + Q] = make_float2(e[k + Q].x + d.y, e[k + Q].y - d.x);       // E - i d
+      v[k + 3 * Q] = make_float2(e[k + Q].x - d.y, e[k + Q].y + d.x);   // E + i d
     }
   }
 }
